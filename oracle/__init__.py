@@ -53,16 +53,22 @@ def build(force=False):
 _lib = None
 
 
+def load(path):
+    """Load a compiled oracle library (the default one, or a copy built elsewhere by a test)."""
+    L = ctypes.CDLL(path)
+    d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int32
+    P = ctypes.POINTER(ctypes.c_double)
+    L.foa_oracle_first.argtypes = [i64, P, P, P, P]
+    L.foa_oracle_first.restype = ctypes.c_int
+    L.foa_oracle_step.argtypes = [i64, i32, P, i64, P, i32, P, i32, P, d, ctypes.c_int, P]
+    L.foa_oracle_step.restype = ctypes.c_int
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int32
-        P = ctypes.POINTER(ctypes.c_double)
-        _lib.foa_oracle_first.argtypes = [i64, P, P, P, P]
-        _lib.foa_oracle_first.restype = ctypes.c_int
-        _lib.foa_oracle_step.argtypes = [i64, i32, P, i64, P, i32, P, i32, P, d, ctypes.c_int, P]
-        _lib.foa_oracle_step.restype = ctypes.c_int
+        _lib = load(build())
     return _lib
 
 
@@ -83,7 +89,8 @@ def auto_rank_tol(storage, n_snapshots):
 class FoaOracle:
     """Streaming FOA-based DMD state (H, V, beta, q) of Algorithm 3 in FP64 on the host."""
 
-    def __init__(self, n, k_max, breakdown_tol=None, storage="f64", reorth=1):
+    def __init__(self, n, k_max, breakdown_tol=None, storage="f64", reorth=1, library=None):
+        self._L = library
         self.n, self.k_max = int(n), int(k_max)
         self.storage = storage
         self.tol = default_breakdown_tol(storage) if breakdown_tol is None else float(breakdown_tol)
@@ -107,7 +114,7 @@ class FoaOracle:
             return "full", float("nan"), float("nan")
         if not np.all(np.isfinite(x)):
             return "nonfinite", float("nan"), float("nan")
-        L = lib()
+        L = self._L or lib()
         if self.q == 0:
             nrm = ctypes.c_double(0.0)
             st = L.foa_oracle_first(self.n, _ptr(self.V), _ptr(self.B), _ptr(x), ctypes.byref(nrm))
@@ -231,10 +238,10 @@ def mode_order(lam, c):
     return np.lexsort((-lam.imag, -np.abs(lam), -key))
 
 
-def run(X, k_max=None, breakdown_tol=None, storage="f64", reorth=1):
+def run(X, k_max=None, breakdown_tol=None, storage="f64", reorth=1, library=None):
     """Algorithm 1 (batch form) as a loop of streaming updates; returns the oracle state."""
     n, N = X.shape
-    o = FoaOracle(n, k_max or N, breakdown_tol, storage, reorth)
+    o = FoaOracle(n, k_max or N, breakdown_tol, storage, reorth, library)
     for t in range(N):
         st, _, _ = o.push(X[:, t])
         if st != "ok":
