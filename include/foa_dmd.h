@@ -1,0 +1,240 @@
+/*
+ * foa_dmd.h -- C ABI of the GB300 streaming FOA-based DMD library.
+ *
+ * The library implements the modified Full Orthogonalization Arnoldi (FOA) update of
+ * FOA-based projected DMD (Anantharamu & Mahesh, arXiv:1805.05821, Sec. 3.1, Algorithms 1,
+ * 3 and 4) and the on-demand extraction of DMD eigenvalues, error indicators, amplitudes and
+ * modes (Algorithm 1 steps 20-29, Sec. 3.2.2-3.2.4).  Every step runs in CUDA kernels built
+ * for sm_103a; there is no CPU fallback.  If no suitable GPU is present, foa_dmd_create
+ * returns FOA_DMD_ECUDA.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a status (foa_dmd_status).  On any status other than FOA_DMD_OK and
+ *    FOA_DMD_EBREAKDOWN the stream state (H, V, beta, q) is unchanged.
+ *  - "device" pointers are CUDA global memory of the current device; "host" pointers are
+ *    ordinary (or pinned) host memory.  The caller owns every buffer it passes; the library
+ *    keeps no pointer to it after the call's stream work has completed.
+ *  - Work is issued on the handle's stream (foa_dmd_opts.cuda_stream).  Calls that take a
+ *    host output pointer synchronise that stream before returning; the others are
+ *    asynchronous and stream-ordered.
+ *  - A handle is not thread-safe.  Different handles are independent.
+ *  - Storage dtype: snapshots and the basis V are stored in FP64, FP32 or BF16.  H-bar, beta
+ *    and all coefficient arithmetic are FP64 in every case.  With FP32 or BF16 storage the
+ *    streaming dot products use FP32 products with FP64 accumulation of blocked partial sums.
+ */
+#ifndef FOA_DMD_H
+#define FOA_DMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct foa_dmd foa_dmd_t;
+typedef struct foa_dmd_batch foa_dmd_batch_t;
+
+/* storage dtype of snapshots and of V */
+typedef enum { FOA_DMD_F64 = 0, FOA_DMD_F32 = 1, FOA_DMD_BF16 = 2 } foa_dmd_dtype;
+
+typedef enum {
+  FOA_DMD_OK = 0,
+  FOA_DMD_EINVAL = 1,      /* bad argument (null pointer, size, misaligned buffer, ...) */
+  FOA_DMD_ENOMEM = 2,      /* device or host allocation failed */
+  FOA_DMD_ECUDA = 3,       /* CUDA error, or no sm_103 device */
+  FOA_DMD_EFULL = 4,       /* q == k_max: no room for another basis vector */
+  FOA_DMD_EBREAKDOWN = 5,  /* snapshot is linearly dependent on the previous ones (Sec. 3.2.4:
+                              h_{j+1,j} = 0); H-bar column j is recorded with h_{j+1,j} = 0,
+                              the stream freezes and the j x j projected matrix is exact */
+  FOA_DMD_ESTOPPED = 6,    /* push after a breakdown */
+  FOA_DMD_ENONFINITE = 7,  /* snapshot holds NaN or Inf; state unchanged */
+  FOA_DMD_ETIMEOUT = 8,    /* a bounded device wait ran out; the handle should be destroyed */
+  FOA_DMD_EIO = 9,         /* checkpoint file error or checksum mismatch */
+  FOA_DMD_ENOCONV = 10     /* the device eigensolver did not converge */
+} foa_dmd_status;
+
+typedef struct {
+  int32_t reorth;          /* 1 (default): classical Gram-Schmidt with one reorthogonalization
+                              (CGS2, Alg. 1 steps 10-14); 0: one classical Gram-Schmidt pass */
+  double breakdown_tol;    /* breakdown when h_{j+1,j} beta_{j,j} <= tol * ||x||_2; <= 0 selects
+                              the default sqrt(u) of the storage dtype (2^-26.5, 2^-12, 2^-4) */
+  int32_t indicator_every; /* 0 (default): push reports h_{j+1,j} only; m > 0: every m-th push
+                              also runs the eigensolve and reports the error indicator */
+  int32_t n_lead;          /* number of leading modes (by |amplitude|) the scheduled indicator
+                              takes its maximum over; default 32 */
+  double indicator_rank_tol; /* rank_tol for the scheduled eigensolve (0: no truncation,
+                                < 0: automatic, as for foa_dmd_eig) */
+  void *cuda_stream;       /* cudaStream_t for all work of the handle; NULL = default stream */
+} foa_dmd_opts;
+
+/* Fill opts with the defaults listed above. */
+void foa_dmd_opts_default(foa_dmd_opts *opts);
+
+/* Result of one push. */
+typedef struct {
+  double h_last;     /* h_{q,q-1} of this push (beta_{1,1} = ||x|| on the first push) */
+  double indicator;  /* max over the n_lead leading modes of the error indicator of Sec. 3.2.3
+                        (Eq. errordmdvec: |h_{m+1,m}| |e_m^T z_i|, or its truncated form);
+                        NaN when this push did not schedule an eigensolve */
+  double x_norm;     /* ||x||_2 */
+  int32_t q;         /* number of basis vectors after the push */
+  int32_t status;    /* foa_dmd_status of this push */
+} foa_dmd_push_info;
+
+/*
+ * Create a stream of snapshots of length n with room for k_max snapshots
+ * (2 <= k_max <= 512).  Allocates V (n x k_max, storage dtype, row-tiled), H-bar and beta
+ * (k_max x k_max, FP64) and scratch on the current device (Alg. 4 step 2 done once, at the
+ * maximum size).  opts may be NULL (defaults).  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int foa_dmd_create(int64_t n, int32_t k_max, int32_t dtype, const foa_dmd_opts *opts,
+                   foa_dmd_t **out);
+
+/*
+ * Push one snapshot: Algorithm 4 with p = 1 (Alg. 1 steps 2-3 for the first snapshot, steps
+ * 5-18 otherwise).  x_dev: device, n contiguous elements of the handle's dtype, 16-byte
+ * aligned.  info: host; NULL makes the call fully asynchronous (no synchronisation), and
+ * errors found on the device are then reported by the next synchronising call.  The first
+ * push of a stream always synchronises.  Errors: EINVAL, EFULL, EBREAKDOWN, ESTOPPED,
+ * ENONFINITE, ETIMEOUT, ECUDA.
+ */
+int foa_dmd_push(foa_dmd_t *h, const void *x_dev, foa_dmd_push_info *info);
+
+/*
+ * Push p snapshots, the columns of X_dev (device, column-major, leading dimension ld >= n,
+ * ld a multiple of 16 bytes / element size): Algorithm 4 with batch p.  The arithmetic is
+ * bitwise identical to p calls of foa_dmd_push (Sec. 3.1: the streaming and batch forms carry
+ * out the same floating-point operations in the same order).  infos: host array of p, or
+ * NULL (asynchronous).  Stops at the first push whose status is not OK.
+ */
+int foa_dmd_push_batch(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld,
+                       foa_dmd_push_info *infos);
+
+/*
+ * Push one snapshot held in host memory: copies x_host (n elements of the handle's dtype;
+ * pinned memory from foa_dmd_host_alloc gives full copy bandwidth) to a device staging
+ * buffer on the handle's stream, then pushes it as foa_dmd_push does.  The call returns once
+ * the copy is enqueued; x_host must stay valid until the handle's stream has passed the copy
+ * (any later synchronising call, or foa_dmd_sync).
+ */
+int foa_dmd_push_host(foa_dmd_t *h, const void *x_host, foa_dmd_push_info *info);
+
+/* Wait for the handle's stream and return the status of the most recent push. */
+int foa_dmd_sync(foa_dmd_t *h, foa_dmd_push_info *info);
+
+/*
+ * Eigen-decomposition of the projected matrix (Alg. 1 steps 20-29, Alg. 3 steps 5-14), all
+ * on the device in FP64:
+ *   m = q-1 (or q after a breakdown), H_m = H-bar(1:m,1:m);
+ *   rank_tol > 0: SVD beta_m = U Sigma W^T, r = #{sigma_i > rank_tol sigma_1},
+ *                 G = U_r^T H_m U_r;  rank_tol < 0: the same with rank_tol = N eps(dtype)
+ *                 (the numerical-rank rule of Sec. 4.1 with N = m+1 snapshots);
+ *   rank_tol == 0: no truncation, U_r = I, G = H_m;
+ *   (lambda_i, z_i) = eig(G) with ||z_i|| = 1, largest-magnitude entry real positive;
+ *   indicators (Sec. 3.2.3): |h_{m+1,m}| |e_m^T z_i|, truncated
+ *                 ||[(I - U_r U_r^T) H_m U_r z_i ; h_{m+1,m} e_m^T U_r z_i]||;
+ *   amplitudes c (Sec. 3.2.4, Eqs. exrecon/exreconwrt): [z] c = beta_11 U_r^T e_1;
+ *   order: |c| descending, then |lambda| descending, then Im(lambda) descending
+ *   (a conjugate pair shares the larger |c|, so its +Im member comes first);
+ *   modes (Alg. 1 step 26): Phi_i = V_{1:m} U_r z_i for the first n_modes in that order.
+ * Results go to the caller's buffers in res (see foa_dmd_eig_result).  Synchronises.
+ * Errors: EINVAL (m < 1, cap too small, bad phi buffer), ENOCONV, ECUDA.
+ */
+typedef struct {
+  /* inputs */
+  int32_t cap;        /* capacity (entries) of each host array below; must be >= r */
+  int32_t n_modes;    /* number of leading modes to form into phi_dev (0: no modes) */
+  void *phi_dev;      /* device, n x (2 n_modes), column-major, leading dimension ld_phi
+                         (>= n, 16-byte multiple): column 2i = Re Phi_i, column 2i+1 = Im Phi_i;
+                         FP64 for FP64 storage, FP32 otherwise */
+  int64_t ld_phi;
+  double *vec_re, *vec_im; /* optional host (m x vec_cols, leading dimension m): U_r z_i */
+  int32_t vec_cols;
+  /* outputs */
+  int32_t m;          /* size of the projected matrix */
+  int32_t r;          /* truncated rank (m without truncation) */
+  double *lam_re, *lam_im;     /* host, cap entries: eigenvalues, in the order above */
+  double *indicator;           /* host, cap: error indicators */
+  double *amp_re, *amp_im;     /* host, cap: amplitudes c_i */
+  double *sigma;               /* optional host, cap: singular values of beta_m (truncation) */
+  double h_last;               /* h_{m+1,m} */
+} foa_dmd_eig_result;
+
+int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *res);
+
+/*
+ * Copy the FP64 state to host buffers (synchronises): q, stopped flag, H-bar and beta as
+ * k_max x k_max column-major arrays with leading dimension ld >= k_max (either may be NULL).
+ */
+int foa_dmd_get_state(foa_dmd_t *h, int32_t *q, int32_t *stopped, double *Hbar, double *beta,
+                      int32_t ld);
+
+/*
+ * Copy basis columns col0 .. col0+ncols-1 of V into dst_dev (device, n x ncols column-major,
+ * leading dimension ld >= n, storage dtype).  V itself is kept row-tiled: rows are grouped in
+ * tiles of 32, and each tile stores its k_max columns contiguously, so one push reads every
+ * tile's leading q columns as a single contiguous block.
+ */
+int foa_dmd_get_basis(foa_dmd_t *h, int32_t col0, int32_t ncols, void *dst_dev, int64_t ld);
+
+/* Discard all snapshots (q = 0, not stopped); buffers are kept. */
+int foa_dmd_reset(foa_dmd_t *h);
+
+/*
+ * Checkpoint: the stream state of Algorithm 3 is exactly (H, V, beta, q).  save writes a
+ * header (magic, version, n, k_max, dtype, q, stopped), H-bar, beta and the q basis columns
+ * in storage dtype, with an FNV-1a checksum; load recreates a handle from it.  Pushing after
+ * load gives bitwise the same results as an uninterrupted run.  Errors: EIO, ENOMEM, ECUDA.
+ */
+int foa_dmd_save(foa_dmd_t *h, const char *path);
+int foa_dmd_load(const char *path, const foa_dmd_opts *opts, foa_dmd_t **out);
+
+/* Free all resources of the handle (synchronises its stream). NULL is ignored. */
+void foa_dmd_destroy(foa_dmd_t *h);
+
+/* Static string for a status code. */
+const char *foa_dmd_strerror(int status);
+
+/*
+ * Kernel timing.  While enabled, every streaming-pass launch of the handle is bracketed by
+ * CUDA events on the handle's stream.  foa_dmd_profile_read synchronises and returns, per
+ * kernel kind (0: pass A = Alg. 1 steps 9-10, 1: pass B = steps 11-12, 2: pass C = steps
+ * 13-15, 3: column write of step 15), the summed event time in ms, the launch count and the
+ * algorithmic bytes those launches had to move, then clears the counters.
+ */
+typedef struct {
+  double ms[4];
+  double bytes[4];
+  int64_t launches[4];
+} foa_dmd_kernel_stats;
+
+int foa_dmd_profile(foa_dmd_t *h, int enable);
+int foa_dmd_profile_read(foa_dmd_t *h, foa_dmd_kernel_stats *stats);
+
+/* Pinned host memory for foa_dmd_push_host (cudaHostAlloc / cudaFreeHost). */
+int foa_dmd_host_alloc(size_t bytes, void **ptr);
+int foa_dmd_host_free(void *ptr);
+
+/*
+ * Many independent streams of uneven n and k_max advanced together (all FP32 or all BF16
+ * storage).  batch_push advances every stream whose x pointer is non-NULL by one push
+ * (Algorithm 4, p = 1 each) in a single persistent kernel launch; streams have their own
+ * H-bar, beta, V and q.  x_dev: DEVICE array of S device pointers.  h_last_dev: device array
+ * of S doubles receiving h_{q,q-1} of each stream (NaN for inactive or failed streams).
+ * Graph-capturable: all per-push decisions are read from device memory.
+ * Per-stream statuses are read with foa_dmd_batch_get_state.
+ */
+int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *k_max, int32_t dtype,
+                         const foa_dmd_opts *opts, foa_dmd_batch_t **out);
+int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, double *h_last_dev);
+int foa_dmd_batch_get_state(foa_dmd_batch_t *b, int32_t s, int32_t *q, int32_t *status,
+                            double *Hbar, double *beta, int32_t ld);
+int foa_dmd_batch_get_basis(foa_dmd_batch_t *b, int32_t s, int32_t col0, int32_t ncols,
+                            void *dst_dev, int64_t ld);
+void foa_dmd_batch_destroy(foa_dmd_batch_t *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FOA_DMD_H */

@@ -1,0 +1,70 @@
+// Host-side handle of one snapshot stream and helpers shared by the API translation units.
+#pragma once
+#include <vector>
+
+#include "internal.cuh"
+
+namespace foa {
+
+// Launch-geometry knobs of the streaming passes (set per handle; the autotuner may change them).
+struct Geometry {
+  int64_t stage_bytes = 32 * 1024;     // target bytes of V per pipeline stage
+  int64_t smem_budget = 200 * 1024;    // shared memory one CTA may use
+  int64_t inflight_bytes = 96 * 1024;  // bytes of V each CTA keeps in flight
+  int max_ctas_per_sm = 2;
+};
+
+struct EventPair {
+  cudaEvent_t start, stop;
+  int kind;
+  double bytes;
+};
+
+struct EigWork;  // device workspace of the eigensolver (eig.cu)
+
+}  // namespace foa
+
+struct foa_dmd {
+  int64_t n = 0;
+  int kmax = 0;
+  int dtype = 0;
+  int ntiles = 0;
+  int64_t nrows = 0;
+  int sms = 0;
+  foa_dmd_opts opts;
+  cudaStream_t stream = nullptr;
+  double tol = 0.0;
+  foa::Geometry geom;
+  void *V = nullptr;
+  void *w = nullptr;
+  double *H = nullptr, *B = nullptr, *pre = nullptr, *hvec = nullptr, *svec = nullptr;
+  double *partials = nullptr, *gpart = nullptr;
+  uint32_t *gcount = nullptr;
+  foa::DevState *st = nullptr;
+  foa_dmd_push_info *info_dev = nullptr;
+  void *stage_x = nullptr;
+  int stage_flip = 0;
+  int q_host = 0;
+  bool stopped_host = false;
+  int pushes_host = 0;
+  bool prof = false;
+  size_t prof_used = 0;
+  std::vector<foa::EventPair> events;
+  foa::EigWork *eig = nullptr;
+};
+
+namespace foa {
+int cuda_status(cudaError_t e);
+int sync_state(foa_dmd *h, foa_dmd_push_info *info);
+int check_device(int *sms);
+double default_tol(int dtype);
+int max_kmax_for(int dtype);
+bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n, int ntiles, int sms, PassArgs &a,
+                    int &grid);
+int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *coef, bool batch,
+                  foa_dmd_push_info *info_out);
+int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_out);
+// eigen path (eig.cu)
+void eig_free(foa_dmd *h);
+int maybe_indicator(foa_dmd *h);  // the indicator schedule of foa_dmd_opts.indicator_every
+}  // namespace foa

@@ -1,0 +1,262 @@
+// Host orchestration of the device eigen path: foa_dmd_eig and the push-time indicator schedule.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "api_internal.cuh"
+#include "eig_internal.cuh"
+
+namespace foa {
+
+static constexpr int kVecGridMax = 64;  // CTAs of the inverse-iteration kernel (each owns LU scratch)
+
+void eig_free(foa_dmd *h) {
+  EigWork *w = h->eig;
+  if (!w) return;
+  void *ptrs[] = {w->A,  w->U,  w->sig_raw, w->sig, w->G,      w->Q,     w->T,     w->Aqr,   w->wr,
+                  w->wi, w->yr, w->yi,      w->ysr, w->ysi,    w->ind,   w->amp_re, w->amp_im, w->out,
+                  w->anorm, w->lu, w->tw, w->yplanes, w->perm, w->isc, w->gb};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete w;
+  h->eig = nullptr;
+}
+
+static int eig_alloc(foa_dmd *h) {
+  if (h->eig) return FOA_DMD_OK;
+  EigWork *w = new (std::nothrow) EigWork();
+  if (!w) return FOA_DMD_ENOMEM;
+  h->eig = w;
+  const int K = h->kmax;
+  w->K = K;
+  w->vgrid = kVecGridMax;
+  const size_t K2 = size_t(K) * K * 8, K1 = size_t(K) * 8;
+  cudaError_t e = cudaSuccess;
+#define AL(p, b)                                          \
+  do {                                                    \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(p), (b)); \
+  } while (0)
+  AL(w->A, K2); AL(w->U, K2); AL(w->sig_raw, K1); AL(w->sig, K1); AL(w->G, K2); AL(w->Q, K2); AL(w->T, K2);
+  AL(w->Aqr, K2); AL(w->wr, K1); AL(w->wi, K1); AL(w->yr, K2); AL(w->yi, K2); AL(w->ysr, K2); AL(w->ysi, K2);
+  AL(w->ind, K1); AL(w->amp_re, K1); AL(w->amp_im, K1); AL(w->out, OUT_N * K1); AL(w->anorm, 8);
+  AL(w->lu, size_t(w->vgrid) * 2 * K2); AL(w->tw, size_t(w->vgrid) * 2 * K1); AL(w->yplanes, 2 * K2);
+  AL(w->perm, size_t(K) * 4); AL(w->isc, ISC_N * 4); AL(w->gb, sizeof(GridBar));
+#undef AL
+  if (e == cudaSuccess) e = cudaMemset(w->gb, 0, sizeof(GridBar));
+  if (e == cudaSuccess) e = cudaMemset(w->isc, 0, ISC_N * 4);
+  if (e != cudaSuccess) {
+    eig_free(h);
+    return cuda_status(e);
+  }
+  return FOA_DMD_OK;
+}
+
+static double eps_of(int dtype) {
+  return dtype == FOA_DMD_F64 ? std::ldexp(1.0, -52) : dtype == FOA_DMD_F32 ? std::ldexp(1.0, -23)
+                                                                              : std::ldexp(1.0, -7);
+}
+
+struct EigOut {
+  int m = 0, r = 0, status = FOA_DMD_OK;
+  double hlast = 0.0;
+  std::vector<double> out;  // OUT_N x K
+};
+
+// Run the eigen path up to the sorted scalars and y columns (device); copies the scalars back.
+static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
+  int rc = sync_state(h, nullptr);
+  if (rc) return rc;
+  const int q = h->q_host;
+  const int m = h->stopped_host ? q : q - 1;
+  if (m < 1) return FOA_DMD_EINVAL;
+  rc = eig_alloc(h);
+  if (rc) return rc;
+  EigWork *w = h->eig;
+  const int K = h->kmax;
+  cudaStream_t s = h->stream;
+  double hb[2];
+  cudaError_t e = cudaMemcpyAsync(&hb[0], h->H + m + int64_t(m - 1) * K, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb[1], h->B, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->isc, 0, ISC_N * 4, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const double hlast = (m < K) ? hb[0] : 0.0;
+  const double b11 = hb[1];
+  double tol = 0.0;
+  if (rank_tol > 0.0) tol = rank_tol;
+  else if (rank_tol < 0.0) tol = (m + 1) * eps_of(h->dtype);
+  const bool trunc = tol > 0.0;
+  int r = m;
+  if (trunc) {
+    // cooperative one-sided Jacobi SVD of beta_m
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_jacobi_kernel, 256, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    int grid = h->sms * (per_sm < 1 ? 1 : (per_sm > 1 ? 1 : per_sm));
+    const int need = ((m + 1) / 2 + 7) / 8;  // one warp per pair
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    const double *Bp = h->B;
+    int ldb = K, mm = m, lda = K, sweeps = 30, *iscp = w->isc;
+    double *Ap = w->A, *sigp = w->sig_raw, jt = 4.0 * std::ldexp(1.0, -53) * std::sqrt(double(m));
+    GridBar *gbp = w->gb;
+    void *args[] = {&Bp, &ldb, &mm, &Ap, &lda, &sigp, &iscp, &gbp, &sweeps, &jt};
+    e = cudaLaunchCooperativeKernel((void *)svd_jacobi_kernel, grid, 256, args, 0, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    svd_finish_kernel<<<1, 512, size_t(m) * 12 + 64, s>>>(w->A, K, m, w->sig_raw, w->U, w->sig, w->isc, tol);
+    int iscv[ISC_N];
+    e = cudaMemcpyAsync(iscv, w->isc, sizeof(iscv), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (iscv[ISC_ERR]) return iscv[ISC_ERR];
+    r = iscv[ISC_R];
+    project_t_kernel<<<h->sms * 2, 256, 0, s>>>(h->H, K, m, w->U, K, w->isc, w->T, K);
+    project_g_kernel<<<h->sms * 2, 256, 0, s>>>(w->U, K, m, w->isc, w->T, K, w->G, K);
+    hessenberg_kernel<<<1, 512, size_t(r) * 8 + 32 * 8, s>>>(w->G, K, w->Q, K, w->isc);
+  } else {
+    copy_h_kernel<<<h->sms, 256, 0, s>>>(h->H, K, m, w->G, K, w->isc);
+  }
+  anorm_kernel<<<1, 512, 0, s>>>(w->G, K, w->isc, w->anorm);
+  e = cudaMemcpyAsync(w->Aqr, w->G, size_t(K) * K * 8, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const size_t qr_smem = size_t(r) * r * 8;
+  const bool use_smem = qr_smem <= 200 * 1024;
+  if (use_smem) {
+    e = cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  hqr_kernel<<<1, 512, use_smem ? qr_smem : 0, s>>>(w->Aqr, K, w->isc, w->wr, w->wi, w->isc, use_smem ? 1 : 0);
+  EigArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Hs = w->G;
+  a.Q = w->Q;
+  a.U = w->U;
+  a.H = h->H;
+  a.ldH = K;
+  a.wr = w->wr;
+  a.wi = w->wi;
+  a.anorm = w->anorm;
+  a.lu = w->lu;
+  a.tw = w->tw;
+  a.yr = w->yr;
+  a.yi = w->yi;
+  a.ysr = w->ysr;
+  a.ysi = w->ysi;
+  a.ind = w->ind;
+  a.amp_re = w->amp_re;
+  a.amp_im = w->amp_im;
+  a.out = w->out;
+  a.perm = w->perm;
+  a.isc = w->isc;
+  a.ld = K;
+  a.m = m;
+  a.have_q = trunc ? 1 : 0;
+  a.have_u = trunc ? 1 : 0;
+  a.hlast = hlast;
+  a.b11 = b11;
+  const int vgrid = r < w->vgrid ? r : w->vgrid;
+  const size_t vsmem = (size_t(r) * 10 + size_t(r + 1) / 2 + 64) * 8;
+  vectors_kernel<<<vgrid, 256, vsmem, s>>>(a);
+  if (nsel > r) nsel = r;
+  order_kernel<<<1, 512, size_t(r) * 20 + 64, s>>>(a, nsel);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  res.out.resize(size_t(OUT_N) * K);
+  int iscv[ISC_N];
+  e = cudaMemcpyAsync(res.out.data(), w->out, res.out.size() * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(iscv, w->isc, sizeof(iscv), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (iscv[ISC_ERR]) return iscv[ISC_ERR];
+  res.m = m;
+  res.r = r;
+  res.hlast = hlast;
+  res.status = iscv[ISC_STATUS];
+  return res.status;
+}
+
+// interleave the sorted y columns into real planes [Re y_0, Im y_0, Re y_1, ...] (m x 2 ncols)
+__global__ void planes_kernel(const double *ysr, const double *ysi, int ld, int m, int ncols, double *Y) {
+  const int64_t total = int64_t(m) * ncols;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int c = int(t / m), i = int(t % m);
+    Y[i + int64_t(2 * c) * ld] = ysr[i + int64_t(c) * ld];
+    Y[i + int64_t(2 * c + 1) * ld] = ysi[i + int64_t(c) * ld];
+  }
+}
+
+int maybe_indicator(foa_dmd *h) {
+  h->pushes_host += 1;
+  const int every = h->opts.indicator_every;
+  if (every <= 0 || h->pushes_host % every != 0) return FOA_DMD_OK;
+  EigOut res;
+  int rc = run_eig(h, h->opts.indicator_rank_tol, 0, res);
+  if (rc == FOA_DMD_EINVAL) return FOA_DMD_OK;  // fewer than two snapshots: nothing to indicate
+  if (rc) return rc;
+  const int K = h->kmax;
+  const int nl = res.r < h->opts.n_lead ? res.r : h->opts.n_lead;
+  double ind = 0.0;
+  for (int i = 0; i < nl; ++i) ind = std::fmax(ind, res.out[size_t(OUT_IND) * K + i]);
+  cudaError_t e = cudaMemcpyAsync(&h->st->info.indicator, &ind, 8, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return cuda_status(e);
+}
+
+}  // namespace foa
+
+using namespace foa;
+
+extern "C" int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *res) {
+  if (!h || !res) return FOA_DMD_EINVAL;
+  if (!res->lam_re || !res->lam_im || !res->indicator || !res->amp_re || !res->amp_im) return FOA_DMD_EINVAL;
+  if (res->n_modes < 0 || res->vec_cols < 0) return FOA_DMD_EINVAL;
+  if (res->n_modes > 0) {
+    const int es = h->dtype == FOA_DMD_F64 ? 8 : 4;
+    if (!res->phi_dev || res->ld_phi < h->n || ((res->ld_phi * es) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(res->phi_dev) & 15) != 0)
+      return FOA_DMD_EINVAL;
+  }
+  if (res->vec_cols > 0 && (!res->vec_re || !res->vec_im)) return FOA_DMD_EINVAL;
+  EigOut o;
+  const int nsel = res->n_modes > res->vec_cols ? res->n_modes : res->vec_cols;
+  int rc = run_eig(h, rank_tol, nsel, o);
+  res->m = o.m;
+  res->r = o.r;
+  res->h_last = o.hlast;
+  if (rc) return rc;
+  if (o.r > res->cap) return FOA_DMD_EINVAL;
+  const int K = h->kmax;
+  for (int i = 0; i < o.r; ++i) {
+    res->lam_re[i] = o.out[size_t(OUT_LRE) * K + i];
+    res->lam_im[i] = o.out[size_t(OUT_LIM) * K + i];
+    res->indicator[i] = o.out[size_t(OUT_IND) * K + i];
+    res->amp_re[i] = o.out[size_t(OUT_ARE) * K + i];
+    res->amp_im[i] = o.out[size_t(OUT_AIM) * K + i];
+  }
+  EigWork *w = h->eig;
+  cudaError_t e = cudaSuccess;
+  if (res->sigma) {
+    if (rank_tol != 0.0) e = cudaMemcpy(res->sigma, w->sig, size_t(o.r) * 8, cudaMemcpyDeviceToHost);
+    else
+      for (int i = 0; i < o.r; ++i) res->sigma[i] = NAN;
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  const int vc = res->vec_cols < o.r ? res->vec_cols : o.r;
+  if (vc > 0) {
+    e = cudaMemcpy2D(res->vec_re, size_t(o.m) * 8, w->ysr, size_t(K) * 8, size_t(o.m) * 8, vc, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2D(res->vec_im, size_t(o.m) * 8, w->ysi, size_t(K) * 8, size_t(o.m) * 8, vc,
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const int nm = res->n_modes < o.r ? res->n_modes : o.r;
+  if (nm > 0) {
+    planes_kernel<<<h->sms, 256, 0, h->stream>>>(w->ysr, w->ysi, K, o.m, nm, w->yplanes);
+    rc = launch_modes(h, o.m, w->yplanes, K, 2 * nm, res->phi_dev, res->ld_phi);
+    if (rc) return rc;
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return FOA_DMD_OK;
+}

@@ -1,0 +1,409 @@
+// Streaming passes over the basis V for one modified-FOA push (Alg. 1 steps 9-15, Alg. 4
+// steps 17-23).  One templated kernel serves four pass kinds:
+//
+//   PASS_A      w = (x - V beta_pre) / beta_jj  (step 9),  h = V^T w         (step 10), ||x||^2
+//   PASS_B      w = w - V h                     (step 11), s = V^T w         (step 12)
+//   PASS_C      w = w - V s                     (step 14), ||w||^2           (step 15)
+//   PASS_FIRST  ||x||^2 of the first snapshot (Alg. 1 step 2)
+//
+// Layout and schedule.  V is row-tiled: a tile of 32 rows stores its k_max columns one after
+// another (32 contiguous elements per column), so the leading j columns of a tile are one
+// contiguous block of 32*j elements.  A pipeline stage is R consecutive tiles; a producer warp
+// fetches each stage's tiles (and the 32R-row slice of x or w) into a shared-memory ring with
+// one-dimensional bulk async copies completing on mbarriers, and eight consumer warps make two
+// sweeps over the staged block, so V is read from HBM exactly once per pass:
+//   sweep 1 (row-local GEMV-N): thread <- row (x column group), FP32 FMA over blocks of 32
+//           columns folded into FP64, giving the new w for the row;
+//   sweep 2 (GEMV-T split over rows): warp <- columns {warp, warp+8, ...}, lane <- row, one
+//           register accumulator per owned column, flushed with a warp reduction into FP64
+//           every 32 products per lane.
+// Each CTA leaves its FP64 partial vector in global memory; the last CTA of every group of 8
+// CTAs (atomic ticket) sums its group in CTA order, and the last group sums the group partials
+// in group order, so the reduction is deterministic.  That last CTA then applies the scalar
+// part of the step (h, s, h+s, h_{j+1,j}, the beta and H-bar columns, the breakdown test).
+//
+// Every wait is bounded; a timeout records FOA_DMD_ETIMEOUT in the device state and the CTA
+// drains its outstanding copies before it returns.
+#pragma once
+#include "internal.cuh"
+
+namespace foa {
+
+template <typename S, int MODE, int NC>
+__global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
+  using C = typename Compute<S>::T;
+  constexpr bool kFp64 = sizeof(C) == 8;
+  constexpr bool kDots = (MODE == PASS_A || MODE == PASS_B);
+  constexpr bool kNorm = (MODE == PASS_A || MODE == PASS_C || MODE == PASS_FIRST);
+  constexpr bool kBaseX = (MODE == PASS_A || MODE == PASS_FIRST);
+  using BaseT = typename std::conditional<kBaseX, S, C>::type;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState *st = a.st;
+  if (!st->active) return;
+  const int j = (MODE == PASS_FIRST) ? 0 : st->j;
+  if (MODE != PASS_FIRST && (j < 1 || j > a.jcap)) return;
+  if (MODE == PASS_FIRST && st->j != 0) return;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  unsigned char *slots = smem;
+  C *ws = reinterpret_cast<C *>(smem + a.off_ws);
+  C *cf = reinterpret_cast<C *>(smem + a.off_coef);
+  double *dot = reinterpret_cast<double *>(smem + a.off_dot);
+  double *comb = reinterpret_cast<double *>(smem + a.off_comb);
+  double *nrm = reinterpret_cast<double *>(smem + a.off_norm);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + a.off_bar);
+  uint64_t *empty = full + kMaxSlots;
+  volatile int *sflag = reinterpret_cast<volatile int *>(empty + kMaxSlots);  // [0] abort [1] issued [2] last
+
+  const double cscale = (MODE == PASS_A) ? st->inv_bjj : 1.0;
+  if (tid == 0) {
+    for (int i = 0; i < a.slots; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    sflag[0] = 0;
+    sflag[1] = 0;
+    sflag[2] = 0;
+    mbar_fence_init();
+  }
+  for (int c = tid; c < j; c += kThreads) cf[c] = static_cast<C>(a.coef[c]);
+  for (int c = tid; c <= j; c += kThreads) dot[c] = 0.0;
+  __syncthreads();
+
+  const S *Vg = static_cast<const S *>(a.V);
+  const int64_t tile_elems = int64_t(a.kmax) * kTile;
+  const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
+
+  if (warp == kWarps) {
+    // ---------------------------------------------------------------- producer warp
+    if (lane == 0) {
+      const BaseT *baseg = kBaseX ? static_cast<const BaseT *>(a.x) : static_cast<const BaseT *>(a.w);
+      int it = 0;
+      for (int s = blockIdx.x; s < a.nstages; s += gridDim.x, ++it) {
+        const int slot = it % a.slots;
+        if (it >= a.slots) {
+          if (!mbar_wait(&empty[slot], ((it / a.slots) - 1) & 1)) {
+            sflag[0] = 1;
+            atomicExch(&st->err, FOA_DMD_ETIMEOUT);
+            break;
+          }
+        }
+        if (sflag[0]) break;
+        const int t0 = s * a.R;
+        const int nt = min(a.R, a.ntiles - t0);
+        const int64_t r0 = int64_t(t0) * kTile;
+        const bool base_bulk = kBaseX ? (a.x_aligned && r0 + int64_t(nt) * kTile <= a.n) : true;
+        const uint32_t bbytes = base_bulk ? uint32_t(nt) * kTile * sizeof(BaseT) : 0u;
+        unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
+        mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
+        if (tile_bytes) {
+          for (int k = 0; k < nt; ++k)
+            bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
+        }
+        if (bbytes) bulk_g2s(dst + a.base_off, baseg + r0, bbytes, &full[slot]);
+        sflag[1] = it + 1;
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumer warps
+  C acc[kDots ? NC : 1];
+#pragma unroll
+  for (int k = 0; k < (kDots ? NC : 1); ++k) acc[k] = C(0);
+  double nacc = 0.0;
+  int since_flush = 0;
+  int it = 0;
+  bool aborted = false;
+
+  auto flush = [&]() {
+    if constexpr (kDots) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const int c = warp + kWarps * k;
+        if (c < j) {
+          const C v = warp_sum(acc[k]);
+          if (lane == 0) dot[c] += static_cast<double>(v);
+          acc[k] = C(0);
+        }
+      }
+    }
+  };
+
+  for (int s = blockIdx.x; s < a.nstages; s += gridDim.x, ++it) {
+    const int slot = it % a.slots;
+    const int failed = mbar_wait(&full[slot], (it / a.slots) & 1) ? 0 : 1;
+    if (named_bar_or(2, kConsumers, failed)) {  // every consumer takes the same decision
+      aborted = true;
+      sflag[0] = 1;
+      if (tid == 0) atomicExch(&st->err, FOA_DMD_ETIMEOUT);
+      break;
+    }
+    const int t0 = s * a.R;
+    const int nt = min(a.R, a.ntiles - t0);
+    const int RS = nt * kTile;
+    const int64_t r0 = int64_t(t0) * kTile;
+    const unsigned char *sbase = slots + size_t(slot) * a.slot_bytes;
+    const S *vs = reinterpret_cast<const S *>(sbase);
+    const bool base_bulk = kBaseX ? (a.x_aligned && r0 + int64_t(RS) <= a.n) : true;
+    const BaseT *bs = reinterpret_cast<const BaseT *>(sbase + a.base_off);
+    const BaseT *bg = kBaseX ? static_cast<const BaseT *>(a.x) : static_cast<const BaseT *>(a.w);
+
+    // ---------------- sweep 1: row-local part
+    const int G = (RS >= kConsumers || j == 0) ? 1 : (kConsumers / RS);
+    const int active_rows_threads = (G == 1) ? kConsumers : G * RS;
+    float nstage_f = 0.f;
+    double nstage_d = 0.0;
+    if (tid < active_rows_threads) {
+      const int g = (G == 1) ? 0 : tid / RS;
+      const int cpg = (j + G - 1) / G;
+      const int c0 = g * cpg;
+      const int c1 = min(j, c0 + cpg);
+      for (int row = (G == 1 ? tid : tid % RS); row < RS; row += (G == 1 ? kConsumers : RS)) {
+        const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
+        double accd = 0.0;
+        if constexpr (kFp64) {
+          double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+          int c = c0;
+          for (; c + 4 <= c1; c += 4) {
+            b0 = fma(to_c(vr[(c + 0) * kTile]), cf[c + 0], b0);
+            b1 = fma(to_c(vr[(c + 1) * kTile]), cf[c + 1], b1);
+            b2 = fma(to_c(vr[(c + 2) * kTile]), cf[c + 2], b2);
+            b3 = fma(to_c(vr[(c + 3) * kTile]), cf[c + 3], b3);
+          }
+          for (; c < c1; ++c) b0 = fma(to_c(vr[c * kTile]), cf[c], b0);
+          accd = (b0 + b1) + (b2 + b3);
+        } else {
+          for (int cb = c0; cb < c1; cb += 32) {
+            const int ce = min(c1, cb + 32);
+            float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+            int c = cb;
+            for (; c + 4 <= ce; c += 4) {
+              b0 = fmaf(to_c(vr[(c + 0) * kTile]), cf[c + 0], b0);
+              b1 = fmaf(to_c(vr[(c + 1) * kTile]), cf[c + 1], b1);
+              b2 = fmaf(to_c(vr[(c + 2) * kTile]), cf[c + 2], b2);
+              b3 = fmaf(to_c(vr[(c + 3) * kTile]), cf[c + 3], b3);
+            }
+            for (; c < ce; ++c) b0 = fmaf(to_c(vr[c * kTile]), cf[c], b0);
+            accd += static_cast<double>((b0 + b1) + (b2 + b3));
+          }
+        }
+        if (G > 1) {
+          comb[g * RS + row] = accd;
+        } else {
+          // finish the row here
+          const int64_t r = r0 + row;
+          double base;
+          if (base_bulk) base = static_cast<double>(to_c(bs[row]));
+          else base = (r < a.n) ? static_cast<double>(to_c(bg[r])) : 0.0;
+          if constexpr (MODE == PASS_FIRST) {
+            const C xv = static_cast<C>(base);
+            if constexpr (kFp64) nstage_d += double(xv) * double(xv); else nstage_f = fmaf(xv, xv, nstage_f);
+          } else {
+            const double wnew = (MODE == PASS_A) ? (base - accd) * cscale : (base - accd);
+            const C wc = static_cast<C>(wnew);
+            static_cast<C *>(a.w)[r] = wc;
+            ws[row] = wc;
+            if constexpr (MODE == PASS_A) {
+              const C xv = static_cast<C>(base);
+              if constexpr (kFp64) nstage_d += double(xv) * double(xv); else nstage_f = fmaf(xv, xv, nstage_f);
+            } else if constexpr (MODE == PASS_C) {
+              if constexpr (kFp64) nstage_d += double(wc) * double(wc); else nstage_f = fmaf(wc, wc, nstage_f);
+            }
+          }
+        }
+      }
+    }
+    if (G > 1) {
+      named_bar_sync(1, kConsumers);
+      if (tid < RS) {
+        const int row = tid;
+        double accd = 0.0;
+        for (int g = 0; g < G; ++g) accd += comb[g * RS + row];
+        const int64_t r = r0 + row;
+        double base;
+        if (base_bulk) base = static_cast<double>(to_c(bs[row]));
+        else base = (r < a.n) ? static_cast<double>(to_c(bg[r])) : 0.0;
+        const double wnew = (MODE == PASS_A) ? (base - accd) * cscale : (base - accd);
+        const C wc = static_cast<C>(wnew);
+        static_cast<C *>(a.w)[r] = wc;
+        ws[row] = wc;
+        if constexpr (MODE == PASS_A) {
+          const C xv = static_cast<C>(base);
+          if constexpr (kFp64) nstage_d += double(xv) * double(xv); else nstage_f = fmaf(xv, xv, nstage_f);
+        } else if constexpr (MODE == PASS_C) {
+          if constexpr (kFp64) nstage_d += double(wc) * double(wc); else nstage_f = fmaf(wc, wc, nstage_f);
+        }
+      }
+    }
+    if constexpr (kNorm) nacc += kFp64 ? nstage_d : static_cast<double>(nstage_f);
+    named_bar_sync(1, kConsumers);  // ws complete
+
+    // ---------------- sweep 2: column dot products over the staged rows
+    if constexpr (kDots) {
+      for (int kt = 0; kt < nt; ++kt) {
+        const C wv = ws[kt * kTile + lane];
+        const S *vt = vs + kt * (kTile * j) + lane;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          const int c = warp + kWarps * k;
+          if (c < j) {
+            if constexpr (kFp64) acc[k] = fma(to_c(vt[c * kTile]), wv, acc[k]);
+            else acc[k] = fmaf(to_c(vt[c * kTile]), wv, acc[k]);
+          }
+        }
+      }
+      if constexpr (!kFp64) {
+        since_flush += nt;
+        if (since_flush >= 32) {
+          flush();
+          since_flush = 0;
+        }
+      }
+    }
+    named_bar_sync(1, kConsumers);  // slot and ws free
+    if (tid == 0) mbar_arrive(&empty[slot]);
+  }
+
+  if (aborted) {
+    // wait for the copies already issued into slots this CTA will not consume
+    if (tid == 0) {
+      const int issued = sflag[1];
+      for (int k = it; k < issued; ++k) mbar_wait(&full[k % a.slots], (k / a.slots) & 1);
+    }
+    return;
+  }
+  flush();
+  if constexpr (kNorm) nrm[tid] = nacc;
+  named_bar_sync(1, kConsumers);
+  const int len = j + 1;
+  if (tid == 0) {
+    if constexpr (kNorm) {
+      double t = 0.0;
+      for (int i = 0; i < kConsumers; ++i) t += nrm[i];
+      dot[j] = t;
+    }
+  }
+  named_bar_sync(1, kConsumers);
+  double *mypart = a.partials + size_t(blockIdx.x) * (a.kmax + 1);
+  for (int c = tid; c < len; c += kConsumers) mypart[c] = dot[c];
+  __threadfence();
+  named_bar_sync(1, kConsumers);
+
+  // ---------------- two-level deterministic reduction (last arriving CTA of each group)
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  const int grp = blockIdx.x / kGroup;
+  const int gfirst = grp * kGroup;
+  const int gsize = min(kGroup, int(gridDim.x) - gfirst);
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&a.gcount[grp], 1u);
+    sflag[2] = (t == unsigned(gsize - 1)) ? 1 : 0;
+  }
+  named_bar_sync(1, kConsumers);
+  if (!sflag[2]) return;
+  __threadfence();
+  double *gp = a.gpart + size_t(grp) * (a.kmax + 1);
+  for (int c = tid; c < len; c += kConsumers) {
+    double t = 0.0;
+    for (int b = 0; b < gsize; ++b) t += __ldcg(a.partials + size_t(gfirst + b) * (a.kmax + 1) + c);
+    gp[c] = t;
+  }
+  __threadfence();
+  named_bar_sync(1, kConsumers);
+  if (tid == 0) {
+    a.gcount[grp] = 0u;
+    const unsigned t = atomicAdd(&st->ticket[MODE], 1u);
+    sflag[2] = (t == unsigned(ngroups - 1)) ? 1 : 0;
+  }
+  named_bar_sync(1, kConsumers);
+  if (!sflag[2]) return;
+  __threadfence();
+  for (int c = tid; c < len; c += kConsumers) {
+    double t = 0.0;
+    for (int g = 0; g < ngroups; ++g) t += __ldcg(a.gpart + size_t(g) * (a.kmax + 1) + c);
+    dot[c] = t;
+  }
+  if (tid == 0) st->ticket[MODE] = 0u;
+  named_bar_sync(1, kConsumers);
+
+  // ---------------- scalar part of the step (one CTA)
+  if constexpr (MODE == PASS_A) {
+    for (int c = tid; c < j; c += kConsumers) a.hvec[c] = dot[c];
+    if (tid == 0) st->x_norm = sqrt(dot[j]);
+  } else if constexpr (MODE == PASS_B) {
+    for (int c = tid; c < j; c += kConsumers) {
+      a.svec[c] = dot[c];
+      a.hvec[c] = a.hvec[c] + dot[c];  // step 13: h = h + s
+    }
+  } else if constexpr (MODE == PASS_C) {
+    const double nu = sqrt(dot[j]);
+    const double xn = st->x_norm;
+    const double bjj = st->bjj;
+    int status;
+    if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
+    else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
+    else status = FOA_DMD_OK;
+    const int64_t ld = a.kmax;
+    if (status != FOA_DMD_ENONFINITE) {
+      for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
+    }
+    if (status == FOA_DMD_OK) {
+      // steps 16-18: beta_{i,j+1} = beta_pre_i + h_{i,j} beta_{j,j}; beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}
+      for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
+    }
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      if (status == FOA_DMD_OK) {
+        a.H[j + int64_t(j - 1) * ld] = nu;
+        a.B[j + int64_t(j) * ld] = nu * bjj;
+        st->nu = nu;
+        st->inv_nu = 1.0 / nu;
+        st->q = j + 1;
+      } else if (status == FOA_DMD_EBREAKDOWN) {
+        a.H[j + int64_t(j - 1) * ld] = 0.0;
+        st->stopped = 1;
+      }
+      st->status = status;
+      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+      foa_dmd_push_info inf;
+      inf.h_last = nu;
+      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+      inf.x_norm = xn;
+      inf.q = st->q;
+      inf.status = status;
+      st->info = inf;
+      if (a.info_out) *a.info_out = inf;
+    }
+  } else if constexpr (MODE == PASS_FIRST) {
+    if (tid == 0) {
+      const double b = sqrt(dot[0]);
+      int status;
+      if (!isfinite(b)) status = FOA_DMD_ENONFINITE;
+      else if (!(b > 0.0)) status = FOA_DMD_EBREAKDOWN;
+      else status = FOA_DMD_OK;
+      if (status == FOA_DMD_OK) {
+        a.B[0] = b;  // Alg. 1 step 3
+        st->nu = b;
+        st->inv_nu = 1.0 / b;
+        st->q = 1;
+      } else if (status == FOA_DMD_EBREAKDOWN) {
+        st->stopped = 1;
+      }
+      st->x_norm = b;
+      st->status = status;
+      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+      foa_dmd_push_info inf;
+      inf.h_last = b;
+      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+      inf.x_norm = b;
+      inf.q = st->q;
+      inf.status = status;
+      st->info = inf;
+      if (a.info_out) *a.info_out = inf;
+    }
+  }
+}
+
+}  // namespace foa

@@ -1,0 +1,38 @@
+// Instantiations of the streaming-pass kernel for double storage.
+#include "pass.cuh"
+
+namespace foa {
+
+template <int MODE, int NC>
+static cudaError_t launch_one(const PassArgs &a, int grid, cudaStream_t s) {
+  auto k = pass_kernel<double, MODE, NC>;
+  static bool configured = false;  // per instantiation; the smem limit is the opt-in maximum
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k<<<grid, kThreads, a.smem_total, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_nc(int nc, const PassArgs &a, int grid, cudaStream_t s) {
+  switch (nc) {
+    case 8: return launch_one<MODE, 8>(a, grid, s);
+    case 16: return launch_one<MODE, 16>(a, grid, s);
+    case 32: return launch_one<MODE, 32>(a, grid, s);
+    default: return launch_one<MODE, 64>(a, grid, s);
+  }
+}
+
+cudaError_t launch_pass_f64(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s) {
+  switch (mode) {
+    case PASS_A: return launch_nc<PASS_A>(nc, a, grid, s);
+    case PASS_B: return launch_nc<PASS_B>(nc, a, grid, s);
+    case PASS_C: return launch_one<PASS_C, 8>(a, grid, s);
+    default: return launch_one<PASS_FIRST, 8>(a, grid, s);
+  }
+}
+
+}  // namespace foa
