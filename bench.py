@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Throughput of streaming FOA-based DMD on one GB300 per rank.
+
+Workload: u, v, w, p fields on a 256^3 grid (n = 4 * 256^3 = 67,108,864), N = 384 snapshots
+stored in FP32 (V is 103 GB), 48 damped travelling waves with amplitudes 1 -> 1e-3 plus 1e-7
+relative noise (kappa_2(X) near 1/eps_fp32).  One step is one full streaming run: reset,
+384 pushes (Alg. 4 with p = 1, the error indicator evaluated every 16 pushes over the 32
+leading modes), then the eigen-decomposition with automatic rank truncation and the DMD modes
+Phi for the 32 leading modes (Alg. 1 steps 20-29).  The snapshots are generated on the device
+before timing (103 GB, larger than L2, so no flush is needed between steps).
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
+With torchrun (N > 1 ranks) every rank runs an independent stream (weak scaling, no
+collective on the data path); the reported value is the total over ranks divided by the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "snapshots/s ingested at n=67M,k≤384; HBM GB/s vs peak; eig rel. err vs FP64 oracle"
+UNIT = "snapshots/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, default=256, help="grid points per axis (256 = the full workload)")
+    p.add_argument("--snapshots", type=int, default=384)
+    p.add_argument("--indicator-every", type=int, default=16)
+    p.add_argument("--modes", type=int, default=32)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sample-grid", type=int, default=32, help="grid of the CPU-oracle sample")
+    return p.parse_args()
+
+
+def workload_name(G, N):
+    return f"fields4x{G}^3 n={4 * G ** 3} N={N} FP32 storage, CGS2 push, indicator every 16 over 32 " \
+           f"leading modes, final eig rank_tol=auto + Phi for 32 leading modes"
+
+
+# ------------------------------------------------------------------ distributed helpers
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(units_local, seconds_local, group=None):
+    """Total units over ranks and the slowest rank's time (max), via torch.distributed if active."""
+    import torch
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(seconds_local)], dtype=torch.float64, device=dev)
+        u = torch.tensor([float(units_local)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+        return float(u.item()), float(t.item())
+    return float(units_local), float(seconds_local)
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_uuid=None):
+        self.proc = None
+        self.uuid = gpu_uuid
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd.insert(1, f"--id={self.uuid}")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def pass_kernel_hash():
+    h = hashlib.sha1()
+    for f in ("pass.cuh", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1805_05821_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def traffic_ratio():
+    """DRAM bytes per algorithmic byte of the pass kernel from the committed ncu summary, if it was
+    taken on the current kernel source (its hash is recorded in the summary)."""
+    path = os.path.join(ROOT, "profiles", "pass_kernel_ncu.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    want = pass_kernel_hash()
+    ratio, src = None, None
+    for line in txt.splitlines():
+        if line.startswith("kernel source hash:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram bytes per algorithmic byte:"):
+            ratio = float(line.split(":", 1)[1].strip())
+    return ratio if (ratio is not None and src == want) else None
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(G, N, every, n_modes, full_n):
+    """The FP64 oracle (C push, OpenMP over fixed row blocks; LAPACK eig) on the same generator at
+    a smaller grid: the same N pushes, indicator schedule, truncated eig and modes.  The push
+    cost is linear in n, so snapshots/s at the full n is the measured rate times n_sample/n."""
+    import oracle
+    from paper_1805_05821_gb300 import synth
+    spec = synth.config5(0, G=G, N=N)
+    X = synth.snapshots(spec, np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    o = oracle.FoaOracle(spec.n, N, storage="f32")
+    for t in range(N):
+        st, _, _ = o.push(X[:, t])
+        if st != "ok":
+            break
+        if every and (t + 1) % every == 0 and o.m >= 1:
+            r = o.eig(0.0)
+            _ = float(np.max(r["indicator"][:32]))
+    res = o.eig(oracle.auto_rank_tol("f32", o.m + 1))
+    _ = o.modes(res, min(n_modes, res["r"]))
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    rate = N / dt * (spec.n / full_n)
+    return {"value": rate, "seconds": dt, "n_sample": spec.n, "cores": cores, "X": X, "spec": spec, "res": res,
+            "oracle": o}
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    full_n = 4 * args.grid ** 3
+    vals = []
+    for i in range(args.warmup + args.steps):
+        s = oracle_sample(args.sample_grid, args.snapshots, args.indicator_every, args.modes, full_n)
+        if i >= args.warmup:
+            vals.append(s)
+    v = statistics.median([s["value"] for s in vals])
+    secs = statistics.median([s["seconds"] for s in vals])
+    sample = (f"FP64 C oracle, OpenMP over fixed row blocks, on fields4x{args.sample_grid}^3 (n={vals[0]['n_sample']}), "
+              f"N={args.snapshots}, same indicator schedule, truncated eig and modes; rate scaled by n_sample/n")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 * full_n / vals[0]["n_sample"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(args.grid, args.snapshots)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    world, rank, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1805_05821_gb300 import build, synth
+    from paper_1805_05821_gb300 import foa_dmd as F
+    build.build()
+    G, N = args.grid, args.snapshots
+    spec = synth.config5(0, G=G, N=N)
+    n = spec.n
+    # ---- inputs resident in HBM
+    X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    tabs = torch.from_numpy(np.stack(spec.tables).astype(np.float32)).cuda()
+    coefs = torch.from_numpy(np.ascontiguousarray(np.transpose(spec.T, (2, 0, 1))).astype(np.float32)).cuda()
+    for t in range(N):
+        F.foa_synth_waves(X[t], "f32", n, 3, G, 4, spec.M, tabs, coefs[t], spec.noise_scale, spec.seed_noise, t)
+    torch.cuda.synchronize()
+    opts = F.foa_dmd_opts_default()
+    opts.indicator_every = args.indicator_every
+    opts.n_lead = 32
+    opts.indicator_rank_tol = 0.0
+    h = F.foa_dmd_create(n, N, "f32", opts)
+    ld_phi = (n + 3) // 4 * 4
+    nm = args.modes
+    phi = torch.empty((2 * nm, ld_phi), dtype=torch.float32, device="cuda")
+    L = F.lib()
+
+    def step(src_dev=None, src_host=None):
+        F.foa_dmd_reset(h)
+        for t in range(N):
+            if src_host is not None:
+                st = L.foa_dmd_push_host(h, ctypes.c_void_p(src_host + t * n * 4), None)
+            else:
+                st = L.foa_dmd_push(h, ctypes.c_void_p(src_dev[t].data_ptr()), None)
+            if st != 0:
+                raise RuntimeError(f"push {t}: {F.STATUS.get(st, st)}")
+        return F.foa_dmd_eig(h, -1.0, N, nm, phi, ld_phi, 0)
+
+    for _ in range(args.warmup):
+        res = step(X)
+        assert res["status"] == 0, res
+    F.foa_dmd_profile_read(h)  # clear
+    F.foa_dmd_profile(h, True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    clk = ClockSampler(uuid)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        res = step(X)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    F.foa_dmd_profile(h, False)
+    stats = F.foa_dmd_profile_read(h)
+    secs = e0.elapsed_time(e1) / 1e3
+    units, secs_max = aggregate(N * args.steps, secs)
+    value = units / secs_max
+    # ---- roofline of the dominant kernel (the streaming pass, kinds 0-2)
+    pk = [0, 1, 2]
+    pass_ms = sum(stats["ms"][k] for k in pk)
+    pass_bytes = sum(stats["bytes"][k] for k in pk)
+    pass_launches = sum(stats["launches"][k] for k in pk)
+    achieved = pass_bytes / (pass_ms / 1e3) / 1e9 if pass_ms > 0 else None
+    peak, peak_src = measured_peak()
+    ratio = traffic_ratio()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": (ratio * pass_bytes / pass_launches) if (ratio and pass_launches) else None,
+            "kernel": "pass_kernel (streaming passes A/B/C over V)",
+            "algorithmic_bytes_per_launch": pass_bytes / pass_launches if pass_launches else None,
+            "avg_launch_ms": pass_ms / pass_launches if pass_launches else None,
+            "share_of_step": pass_ms / (secs * 1e3) if secs > 0 else None,
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"}
+    gpu_launches = stats["total_launches"]
+    # planted-truth check of the leading eigenvalues (err against the generating map)
+    lam = res["lam"]
+    planted = spec.lam
+    rel_planted = None
+    if len(lam):
+        from scipy.optimize import linear_sum_assignment
+        lead = lam[:min(32, len(lam))]
+        D = np.abs(lead[:, None] - planted[None, :])
+        ri, ci = linear_sum_assignment(D)
+        rel_planted = float(np.max(D[ri, ci] / np.abs(planted[ci])))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": secs_max * 1e3 / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload_name(G, N), "n": n, "N": N, "l2": "inputs (N x n FP32 snapshots, "
+                      f"{N * n * 4 / 1e9:.0f} GB) exceed L2; no flush needed", "parallelism": "independent stream per GPU"},
+           "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks,
+           "accuracy": {"rank": res["r"], "m": res["m"], "leading32_rel_err_vs_planted": rel_planted}}
+    # ---- end to end through the public API with host buffers (pinned), copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, h, X, n, N, F, L, step, world)
+        X = None
+    out["e2e"] = e2e
+    # ---- CPU oracle baseline (rank 0) and the FP32-vs-FP64 eigenvalue error on that sample
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(args.sample_grid, N, args.indicator_every, nm, n)
+        out["cpu_baseline"] = {"value": s["value"], "unit": UNIT, "cores": s["cores"], "kind": "oracle",
+                               "sample": f"FP64 C oracle (OpenMP, fixed row blocks) on fields4x{args.sample_grid}^3 "
+                                         f"(n={s['n_sample']}), N={N}, same schedule/eig/modes; "
+                                         f"{s['seconds']:.1f} s, rate scaled by n_sample/n"}
+        out["accuracy"].update(sample_eig_accuracy(s, F, torch, N, nm))
+    F.foa_dmd_destroy(h)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def sample_eig_accuracy(s, F, torch, N, nm):
+    """Relative error of the leading eigenvalues of the FP32 GPU path against the FP64 oracle on the
+    same (FP32-rounded) sample inputs."""
+    X = s["X"]
+    n = X.shape[0]
+    Xd = torch.from_numpy(np.ascontiguousarray(X.T).astype(np.float32)).cuda()
+    g = F.FoaDMD(n, N, "f32")
+    for t in range(N):
+        st, _ = g.push(Xd[t], info=False)
+    res = g.eig(-1.0)
+    ro = s["res"]
+    lo = ro["lam"][:nm]
+    lg = res["lam"]
+    from scipy.optimize import linear_sum_assignment
+    D = np.abs(lo[:, None] - lg[None, :])
+    ri, ci = linear_sum_assignment(D)
+    err = float(np.max(D[ri, ci] / np.abs(lo[ri])))
+    g.close()
+    return {"sample_leading32_eig_rel_err_vs_fp64_oracle": err, "sample_rank_gpu": res["r"], "sample_rank_oracle": ro["r"]}
+
+
+def mem_available_bytes():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return 0
+
+
+def run_e2e(args, h, X, n, N, F, L, step, world):
+    import torch
+    nbytes = N * n * 4
+    if mem_available_bytes() < nbytes + 40 * 2 ** 30:
+        return {"value": None, "unit": UNIT, "skipped": "not enough host memory for pinned snapshots"}
+    ptr = F.foa_dmd_host_alloc(nbytes)
+    try:
+        host = np.ctypeslib.as_array(ctypes.cast(ctypes.c_void_p(ptr), ctypes.POINTER(ctypes.c_float)), shape=(N, n))
+        ht = torch.from_numpy(host)
+        for t in range(N):
+            ht[t].copy_(X[t])
+        torch.cuda.synchronize()
+        del X
+        torch.cuda.empty_cache()
+        step(src_host=ptr)  # warm-up
+        k = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(k):
+            res = step(src_host=ptr)
+            d2h += 6 * 8 * res["r"]
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        barrier()
+        units, secs_max = aggregate(N * k, secs)
+        return {"value": units / secs_max, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": d2h // k,
+                "steps": k, "api": "foa_dmd_push_host (pinned host snapshot, copy overlapped) + foa_dmd_eig"}
+    finally:
+        F.foa_dmd_host_free(ptr)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

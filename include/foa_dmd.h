@@ -201,12 +201,14 @@ const char *foa_dmd_strerror(int status);
  * CUDA events on the handle's stream.  foa_dmd_profile_read synchronises and returns, per
  * kernel kind (0: pass A = Alg. 1 steps 9-10, 1: pass B = steps 11-12, 2: pass C = steps
  * 13-15, 3: column write of step 15), the summed event time in ms, the launch count and the
- * algorithmic bytes those launches had to move, then clears the counters.
+ * algorithmic bytes those launches had to move, plus the number of kernels of any kind the
+ * handle launched since the previous read, then clears the counters.
  */
 typedef struct {
   double ms[4];
   double bytes[4];
   int64_t launches[4];
+  int64_t total_launches;
 } foa_dmd_kernel_stats;
 
 int foa_dmd_profile(foa_dmd_t *h, int enable);

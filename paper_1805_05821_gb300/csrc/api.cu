@@ -138,6 +138,11 @@ void free_handle_buffers(foa_dmd *h) {
     cudaEventDestroy(e.start);
     cudaEventDestroy(e.stop);
   }
+  for (int b = 0; b < 2; ++b) {
+    if (h->stage_free[b]) cudaEventDestroy(h->stage_free[b]);
+    if (h->stage_ready[b]) cudaEventDestroy(h->stage_ready[b]);
+  }
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   h->events.clear();
   eig_free(h);
 }
@@ -250,6 +255,7 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
     default: bytes = n * s; kind = 3; break;
   }
   ProfScope ps(h, kind, bytes);
+  h->launches += 1;
   return cuda_status(launch_pass(h->dtype, mode, pass_nc_for(jcap), a, grid, h->stream));
 }
 
@@ -259,6 +265,7 @@ int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_
   const int jcap = h->q_host;
   int rc = cuda_status(launch_prep(h->st, h->H, h->B, h->pre, h->kmax, first ? 1 : 0, jcap, h->stream, batch ? 1 : 0,
                                    info_out));
+  h->launches += 2;  // prep and the column write
   if (rc) return rc;
   if (first) {
     rc = launch_pass_h(h, PASS_FIRST, 0, x, nullptr, batch, info_out);
@@ -422,18 +429,33 @@ extern "C" int foa_dmd_push_host(foa_dmd_t *h, const void *x_host, foa_dmd_push_
   if (h->stopped_host) return FOA_DMD_ESTOPPED;
   if (h->q_host >= h->kmax) return FOA_DMD_EFULL;
   const size_t bytes = size_t(h->n) * dtype_size(h->dtype);
-  cudaError_t e;
+  const size_t slot = size_t(align_up(int64_t(bytes), 256));
+  cudaError_t e = cudaSuccess;
   if (!h->stage_x) {
-    e = cudaMalloc(&h->stage_x, 2 * align_up(int64_t(bytes), 256));
+    e = cudaMalloc(&h->stage_x, 2 * slot);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaEventCreateWithFlags(&h->stage_free[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_ready[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(h->stage_free[b], h->stream);
+    }
     if (e != cudaSuccess) return cuda_status(e);
   }
-  char *buf = static_cast<char *>(h->stage_x) + (h->stage_flip ? align_up(int64_t(bytes), 256) : 0);
+  // Double-buffered staging: the copy of this snapshot (copy stream) overlaps the previous push
+  // (handle stream); a buffer is refilled only after the push that read it has finished.
+  const int b = h->stage_flip;
   h->stage_flip ^= 1;
-  e = cudaMemcpyAsync(buf, x_host, bytes, cudaMemcpyHostToDevice, h->stream);
+  char *buf = static_cast<char *>(h->stage_x) + (b ? slot : 0);
+  e = cudaStreamWaitEvent(h->copy_stream, h->stage_free[b], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(buf, x_host, bytes, cudaMemcpyHostToDevice, h->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->stage_ready[b], h->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->stage_ready[b], 0);
   if (e != cudaSuccess) return cuda_status(e);
   const bool first = h->q_host == 0;
   int rc = enqueue_push(h, buf, false, nullptr);
   if (rc) return rc;
+  e = cudaEventRecord(h->stage_free[b], h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
   rc = maybe_indicator(h);
   if (rc) return rc;
   return finish_push(h, info, first);
@@ -620,6 +642,8 @@ extern "C" int foa_dmd_profile_read(foa_dmd_t *h, foa_dmd_kernel_stats *stats) {
     stats->bytes[k] += h->events[i].bytes;
     stats->launches[k] += 1;
   }
+  stats->total_launches = h->launches;
+  h->launches = 0;
   h->prof_used = 0;
   return FOA_DMD_OK;
 }

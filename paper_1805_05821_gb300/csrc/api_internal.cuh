@@ -44,6 +44,9 @@ struct foa_dmd {
   foa_dmd_push_info *info_dev = nullptr;
   void *stage_x = nullptr;
   int stage_flip = 0;
+  cudaStream_t copy_stream = nullptr;        // host->device snapshot copies (foa_dmd_push_host)
+  cudaEvent_t stage_free[2] = {nullptr, nullptr}, stage_ready[2] = {nullptr, nullptr};
+  int64_t launches = 0;                      // kernels launched by this handle
   int q_host = 0;
   bool stopped_host = false;
   int pushes_host = 0;

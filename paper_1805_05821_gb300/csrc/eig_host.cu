@@ -114,16 +114,18 @@ static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
     project_t_kernel<<<h->sms * 2, 256, 0, s>>>(h->H, K, m, w->U, K, w->isc, w->T, K);
     project_g_kernel<<<h->sms * 2, 256, 0, s>>>(w->U, K, m, w->isc, w->T, K, w->G, K);
     hessenberg_kernel<<<1, 512, size_t(r) * 8 + 32 * 8, s>>>(w->G, K, w->Q, K, w->isc);
+    h->launches += 5;
   } else {
     copy_h_kernel<<<h->sms, 256, 0, s>>>(h->H, K, m, w->G, K, w->isc);
+    h->launches += 1;
   }
   anorm_kernel<<<1, 512, 0, s>>>(w->G, K, w->isc, w->anorm);
   e = cudaMemcpyAsync(w->Aqr, w->G, size_t(K) * K * 8, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
   const size_t qr_smem = size_t(r) * r * 8;
   const bool use_smem = qr_smem <= 200 * 1024;
-  if (use_smem) {
-    e = cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (use_smem && qr_smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
     if (e != cudaSuccess) return cuda_status(e);
   }
   hqr_kernel<<<1, 512, use_smem ? qr_smem : 0, s>>>(w->Aqr, K, w->isc, w->wr, w->wi, w->isc, use_smem ? 1 : 0);
@@ -160,6 +162,7 @@ static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
   vectors_kernel<<<vgrid, 256, vsmem, s>>>(a);
   if (nsel > r) nsel = r;
   order_kernel<<<1, 512, size_t(r) * 20 + 64, s>>>(a, nsel);
+  h->launches += 4;  // anorm, hqr, vectors, order
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   res.out.resize(size_t(OUT_N) * K);
@@ -253,6 +256,7 @@ extern "C" int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *re
   const int nm = res->n_modes < o.r ? res->n_modes : o.r;
   if (nm > 0) {
     planes_kernel<<<h->sms, 256, 0, h->stream>>>(w->ysr, w->ysi, K, o.m, nm, w->yplanes);
+    h->launches += 2;  // planes and the modes GEMM
     rc = launch_modes(h, o.m, w->yplanes, K, 2 * nm, res->phi_dev, res->ld_phi);
     if (rc) return rc;
     e = cudaStreamSynchronize(h->stream);

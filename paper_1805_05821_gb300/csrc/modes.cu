@@ -54,14 +54,14 @@ int launch_modes(foa_dmd *h, int m, const double *Y, int ldy, int ncols, void *p
   cudaError_t e;
   switch (h->dtype) {
     case FOA_DMD_F64:
-      e = cudaFuncSetAttribute(modes_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+      e = cudaFuncSetAttribute(modes_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e == cudaSuccess)
         modes_simt_kernel<double><<<grid, 256, smem, h->stream>>>(static_cast<const double *>(h->V), h->kmax, h->n,
                                                                   h->ntiles, m, Y, ldy, ncols,
                                                                   static_cast<double *>(phi), ld_phi);
       break;
     case FOA_DMD_F32:
-      e = cudaFuncSetAttribute(modes_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+      e = cudaFuncSetAttribute(modes_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
       if (e == cudaSuccess)
         modes_simt_kernel<float><<<grid, 256, smem, h->stream>>>(static_cast<const float *>(h->V), h->kmax, h->n,
                                                                  h->ntiles, m, Y, ldy, ncols,
@@ -69,7 +69,7 @@ int launch_modes(foa_dmd *h, int m, const double *Y, int ldy, int ncols, void *p
       break;
     default:
       e = cudaFuncSetAttribute(modes_simt_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               232448);
+                               int(smem));
       if (e == cudaSuccess)
         modes_simt_kernel<__nv_bfloat16><<<grid, 256, smem, h->stream>>>(
             static_cast<const __nv_bfloat16 *>(h->V), h->kmax, h->n, h->ntiles, m, Y, ldy, ncols,

@@ -49,7 +49,8 @@ class foa_dmd_eig_result(ctypes.Structure):
 
 
 class foa_dmd_kernel_stats(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 4), ("bytes", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4)]
+    _fields_ = [("ms", ctypes.c_double * 4), ("bytes", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4),
+                ("total_launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -240,7 +241,8 @@ def foa_dmd_profile(h, enable):
 def foa_dmd_profile_read(h):
     s = foa_dmd_kernel_stats()
     _check(lib().foa_dmd_profile_read(h, ctypes.byref(s)), "foa_dmd_profile_read")
-    return {"ms": list(s.ms), "bytes": list(s.bytes), "launches": list(s.launches)}
+    return {"ms": list(s.ms), "bytes": list(s.bytes), "launches": list(s.launches),
+            "total_launches": int(s.total_launches)}
 
 
 def foa_dmd_host_alloc(nbytes):

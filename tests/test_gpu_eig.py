@@ -1,0 +1,145 @@
+"""GPU parity of the eigen path (Alg. 1 steps 20-29; Secs. 3.2.2-3.2.4) against the oracle.
+
+Eigenvalues are matched by optimal assignment (several orders are equally valid when |c| ties).
+Tolerance for eigenvalue i: 1e-10 ||H||_2 / s_i with s_i = |y_i^H z_i| the condition of the
+eigenvalue from the oracle's left/right eigenvectors (FP64 storage); indicators, amplitude
+magnitudes and modes are compared after matching.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from gpu_util import match, rel, run_gpu, run_oracle, to_device
+from paper_1805_05821_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1805_05821_gb300 import build
+    build.build()
+
+
+def eig_condition(G):
+    w, vl, vr = scipy.linalg.eig(G, left=True, right=True)
+    s = np.abs(np.sum(np.conj(vl) * vr, axis=0)) / (np.linalg.norm(vl, axis=0) * np.linalg.norm(vr, axis=0))
+    return w, s
+
+
+def check_eigs(res_g, res_o, scale=1e-10):
+    lam_g, lam_o = res_g["lam"], res_o["lam"]
+    assert len(lam_g) == len(lam_o)
+    d, perm = match(lam_o, lam_g)
+    w, s = eig_condition(res_o["G"])
+    # condition numbers in the oracle's order
+    dd, pw = match(lam_o, w)
+    s_o = s[pw]
+    nrm = np.linalg.norm(res_o["G"], 2)
+    assert np.all(d <= scale * nrm / np.maximum(s_o, 1e-300) + 1e-14 * nrm), (d, s_o)
+    return perm
+
+
+def test_eig_breakdown_case():
+    spec = synth.config1(0)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f64")
+    g, _ = run_gpu(Xd, spec.n, 32, "f64")
+    o, _ = run_oracle(Xr, 32, "f64")
+    rg = g.eig(0.0, vec_cols=10)
+    ro = o.eig(0.0)
+    assert rg["status"] == 0 and rg["m"] == 10 and rg["r"] == 10
+    check_eigs(rg, ro)
+    d, _ = match(rg["lam"], spec.lam)
+    assert d.max() < 1e-9
+    np.testing.assert_array_equal(rg["indicator"], 0.0)
+
+
+@pytest.mark.parametrize("N", [6, 25, 60])
+def test_eig_untruncated(N):
+    spec = synth.config2(1, G=64, N=N)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f64")
+    g, _ = run_gpu(Xd, spec.n, N, "f64")
+    o, _ = run_oracle(Xr, N, "f64")
+    rg = g.eig(0.0, vec_cols=N)
+    ro = o.eig(0.0)
+    assert rg["status"] == 0
+    perm = check_eigs(rg, ro)
+    # indicators and amplitude magnitudes of well-conditioned eigenvalues
+    ind_o, ind_g = ro["indicator"], rg["indicator"][perm]
+    amp_o, amp_g = np.abs(ro["amp"]), np.abs(rg["amp"][perm])
+    w, s = eig_condition(ro["G"])
+    _, pw = match(ro["lam"], w)
+    good = s[pw] > 1e-3
+    assert np.all(np.abs(ind_g - ind_o)[good] <= 1e-8 * np.maximum(ind_o[good], 1e-3 * ind_o.max()))
+    assert np.all(np.abs(amp_g - amp_o)[good] <= 1e-7 * np.maximum(amp_o[good], 1e-6 * amp_o.max()))
+    # eigenvectors (U_r z_i), phase-invariant
+    Zo = ro["Y"]
+    Zg = rg["vec"][:, perm]
+    for i in np.where(good)[0]:
+        c = abs(np.vdot(Zo[:, i], Zg[:, i]))
+        assert abs(1 - c) < 1e-8, (i, c)
+
+
+def test_eig_truncated_and_modes():
+    """Rank truncation (Sec. 3.2.2) with rank_tol = 1e-7 on a rank-12 map with 1e-10 noise."""
+    spec = synth.planted(20000, 30, 12, seed=6, noise_rel=1e-10)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f64")
+    g, _ = run_gpu(Xd, spec.n, 30, "f64", breakdown_tol=1e-14)
+    o, _ = run_oracle(Xr, 30, "f64", tol=1e-14)
+    rg = g.eig(1e-7, n_modes=12)
+    ro = o.eig(1e-7)
+    assert rg["status"] == 0
+    assert rg["r"] == ro["r"] == 12
+    np.testing.assert_allclose(rg["sigma"], ro["sigma"][:12], rtol=1e-10)
+    perm = check_eigs(rg, ro, scale=1e-9)
+    d, _ = match(rg["lam"], spec.lam)
+    assert d.max() < 1e-6
+    assert np.all(np.abs(rg["indicator"][perm] - ro["indicator"]) <= 1e-7 * np.abs(ro["indicator"]).max() + 1e-12)
+    Phi_o = o.modes(ro, 12)
+    Phi_g = rg["phi"][:, perm]
+    for i in range(12):
+        c = abs(np.vdot(Phi_o[:, i], Phi_g[:, i])) / (np.linalg.norm(Phi_o[:, i]) * np.linalg.norm(Phi_g[:, i]))
+        assert abs(1 - c) < 1e-8
+
+
+def test_modes_fp32():
+    spec = synth.config2(2, G=64, N=24)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f32")
+    g, _ = run_gpu(Xd, spec.n, 24, "f32")
+    o, _ = run_oracle(Xr, 24, "f32")
+    rg = g.eig(0.0, n_modes=8)
+    ro = o.eig(0.0)
+    assert rg["status"] == 0
+    d, perm = match(ro["lam"], rg["lam"])
+    Phi_o = o.modes(ro, len(ro["lam"]))
+    for k in range(8):
+        i = int(np.where(perm == k)[0][0])
+        a = Phi_o[:, i]
+        b = rg["phi"][:, k]
+        c = abs(np.vdot(a, b)) / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert abs(1 - c) < 1e-3
+
+
+def test_indicator_schedule():
+    """indicator_every = 5: every fifth push reports max over the n_lead leading modes (Sec. 3.2.3)."""
+    spec = synth.config2(3, G=48, N=21)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f64")
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    g = FoaDMD(spec.n, 21, "f64", indicator_every=5, n_lead=4)
+    import oracle as orc
+    oo = orc.FoaOracle(spec.n, 21)
+    for t in range(21):
+        st, inf = g.push(Xd[t])
+        oo.push(Xr[:, t])
+        assert st == 0
+        if (t + 1) % 5 == 0:
+            ro = oo.eig(0.0)
+            want = ro["indicator"][:4].max()
+            assert abs(inf["indicator"] - want) <= 1e-7 * want + 1e-14, (t, inf["indicator"], want)
+        else:
+            assert np.isnan(inf["indicator"])
