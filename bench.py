@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "snapshots/s ingested at n=67M,k≤384; HBM GB/s vs peak; eig rel. err vs FP64 oracle"
 UNIT = "snapshots/s"
 FALLBACK_HBM_GBS = 6800.0
+BREAKDOWN_TOL = 1e-12
 
 
 def parse():
@@ -54,8 +55,8 @@ def parse():
 
 
 def workload_name(G, N):
-    return f"fields4x{G}^3 n={4 * G ** 3} N={N} FP32 storage, CGS2 push, indicator every 16 over 32 " \
-           f"leading modes, final eig rank_tol=auto + Phi for 32 leading modes"
+    return f"fields4x{G}^3 n={4 * G ** 3} N={N} FP32 storage, CGS2 push (breakdown_tol {BREAKDOWN_TOL:g}), " \
+           f"indicator every 16 over 32 leading modes, final eig rank_tol=auto + Phi for 32 leading modes"
 
 
 # ------------------------------------------------------------------ distributed helpers
@@ -175,7 +176,7 @@ def oracle_sample(G, N, every, n_modes, full_n):
     spec = synth.config5(0, G=G, N=N)
     X = synth.snapshots(spec, np.float32).astype(np.float64)
     t0 = time.perf_counter()
-    o = oracle.FoaOracle(spec.n, N, storage="f32")
+    o = oracle.FoaOracle(spec.n, N, breakdown_tol=BREAKDOWN_TOL, storage="f32")
     for t in range(N):
         st, _, _ = o.push(X[:, t])
         if st != "ok":
@@ -244,6 +245,10 @@ def main():
     opts.indicator_every = args.indicator_every
     opts.n_lead = 32
     opts.indicator_rank_tol = 0.0
+    # The workload's snapshots beyond its 96 wave dimensions differ only by 1e-7 noise (kappa_2 near
+    # 1/eps_fp32 on purpose, to exercise rank truncation); the default breakdown test (sqrt(u_fp32))
+    # would stop the stream there, so the run keeps every snapshot.
+    opts.breakdown_tol = BREAKDOWN_TOL
     h = F.foa_dmd_create(n, N, "f32", opts)
     ld_phi = (n + 3) // 4 * 4
     nm = args.modes
@@ -351,7 +356,7 @@ def sample_eig_accuracy(s, F, torch, N, nm):
     X = s["X"]
     n = X.shape[0]
     Xd = torch.from_numpy(np.ascontiguousarray(X.T).astype(np.float32)).cuda()
-    g = F.FoaDMD(n, N, "f32")
+    g = F.FoaDMD(n, N, "f32", breakdown_tol=BREAKDOWN_TOL)
     for t in range(N):
         st, _ = g.push(Xd[t], info=False)
     res = g.eig(-1.0)

@@ -120,6 +120,19 @@ int foa_dmd_push_batch(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld,
  */
 int foa_dmd_push_host(foa_dmd_t *h, const void *x_host, foa_dmd_push_info *info);
 
+/*
+ * Push-time error indicators (foa_dmd_opts.indicator_every = m > 0).  Every m-th push enqueues
+ * the eigensolve of the projected matrix of that moment on a low-priority side stream, where it
+ * overlaps the following pushes (the streaming passes leave one SM free for it).  A push that
+ * asks for its info waits for its own indicator.  This call waits for the side stream and
+ * returns, oldest first, up to cap records not yet read: the 1-based index of the push that
+ * scheduled it (counted since create/reset), the size m of the projected matrix, and the
+ * indicator (max over the n_lead leading modes; NaN if the eigensolve failed).  The device
+ * keeps the last 1024 records.  Indicators assume the preceding asynchronous pushes succeeded.
+ */
+int foa_dmd_indicators(foa_dmd_t *h, int32_t *push_index, int32_t *m, double *value, int32_t cap,
+                       int32_t *count);
+
 /* Wait for the handle's stream and return the status of the most recent push. */
 int foa_dmd_sync(foa_dmd_t *h, foa_dmd_push_info *info);
 

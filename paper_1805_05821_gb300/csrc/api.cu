@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "api_internal.cuh"
+#include "eig_internal.cuh"
 #include "push_kernels.cuh"
 
 using namespace foa;
@@ -41,8 +42,15 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   const int64_t other = align_up(int64_t(R) * kTile * cs, 128) + align_up(int64_t(jcap + 1) * cs, 16) +
                         align_up(int64_t(jcap + 2) * 8, 16) + kConsumers * 8 + kConsumers * 8 + 2 * kMaxSlots * 8 +
                         64;
-  int slots = int((g.smem_budget - other) / slot_bytes);
-  const int want = int((g.inflight_bytes + slot_bytes - 1) / slot_bytes) + 1;
+  // two CTAs per SM for FP32/BF16 while the column accumulators fit in registers (j <= 384) and
+  // two slots fit in half the shared memory; otherwise one CTA per SM with a deeper ring
+  const int nc = pass_nc_for(jcap);
+  const bool two = (cs == 4) && (mode == PASS_C || mode == PASS_FIRST || nc <= 48) &&
+                   (2 * slot_bytes + other <= g.smem_budget2) && g.max_ctas_per_sm >= 2;
+  const int64_t budget = two ? g.smem_budget2 : g.smem_budget;
+  const int64_t inflight = two ? g.inflight_bytes / 2 : g.inflight_bytes;
+  int slots = int((budget - other) / slot_bytes);
+  const int want = int((inflight + slot_bytes - 1) / slot_bytes) + 1;
   if (slots > want) slots = want;
   if (slots > kMaxSlots) slots = kMaxSlots;
   if (slots < 2) return false;
@@ -69,9 +77,7 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   a.n = n;
   a.jcap = jcap;
   a.nstages = (ntiles + R - 1) / R;
-  int per_sm = int(233472 / (a.smem_total + 1024));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > g.max_ctas_per_sm) per_sm = g.max_ctas_per_sm;
+  const int per_sm = two ? 2 : 1;
   grid = a.nstages < sms * per_sm ? a.nstages : sms * per_sm;
   return true;
 }
@@ -225,7 +231,9 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
   PassArgs a;
   memset(&a, 0, sizeof(a));
   int grid = 0;
-  if (!make_pass_geom(h->geom, h->dtype, mode, jcap, h->n, h->ntiles, h->sms, a, grid)) return FOA_DMD_EINVAL;
+  // with an indicator schedule one SM is left to the side-stream eigensolve
+  const int sms = h->sms - (h->opts.indicator_every > 0 ? 1 : 0);
+  if (!make_pass_geom(h->geom, h->dtype, mode, jcap, h->n, h->ntiles, sms, a, grid)) return FOA_DMD_EINVAL;
   a.V = h->V;
   a.x = x;
   a.w = h->w;
@@ -340,6 +348,7 @@ static int finish_push(foa_dmd *h, foa_dmd_push_info *info, bool force_sync) {
   foa_dmd_push_info inf;
   int rc = sync_state(h, &inf);
   if (rc) return rc;
+  if (h->ind_this_push) inf.indicator = latest_indicator(h, false);
   if (info) *info = inf;
   return inf.status < 0 ? FOA_DMD_ECUDA : inf.status;
 }
@@ -492,6 +501,11 @@ extern "C" int foa_dmd_get_basis(foa_dmd_t *h, int32_t col0, int32_t ncols, void
 
 extern "C" int foa_dmd_reset(foa_dmd_t *h) {
   if (!h) return FOA_DMD_EINVAL;
+  if (h->ind_stream) {
+    cudaError_t e0 = cudaStreamSynchronize(h->ind_stream);
+    if (e0 != cudaSuccess) return cuda_status(e0);
+  }
+  h->pushes_host = 0;
   cudaError_t e = cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->H, 0, size_t(h->kmax) * h->kmax * 8, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->B, 0, size_t(h->kmax) * h->kmax * 8, h->stream);
@@ -654,3 +668,26 @@ extern "C" int foa_dmd_host_alloc(size_t bytes, void **ptr) {
 }
 
 extern "C" int foa_dmd_host_free(void *ptr) { return cuda_status(cudaFreeHost(ptr)); }
+
+extern "C" int foa_dmd_indicators(foa_dmd_t *h, int32_t *push_index, int32_t *m, double *value, int32_t cap,
+                                  int32_t *count) {
+  if (!h || !count || cap < 0) return FOA_DMD_EINVAL;
+  *count = 0;
+  if (!h->ind_stream) return FOA_DMD_OK;
+  cudaError_t e = cudaStreamSynchronize(h->ind_stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (h->ind_issued - h->ind_read > kIndRing) h->ind_read = h->ind_issued - kIndRing;
+  std::vector<IndRecord> recs(static_cast<size_t>(kIndRing));
+  e = cudaMemcpy(recs.data(), h->ind_ring, sizeof(IndRecord) * kIndRing, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  int k = 0;
+  for (; h->ind_read < h->ind_issued && k < cap; ++h->ind_read, ++k) {
+    const IndRecord &r = recs[size_t(h->ind_read % kIndRing)];
+    if (push_index) push_index[k] = r.push;
+    if (m) m[k] = r.m;
+    if (value) value[k] = r.value;
+  }
+  h->ind_pending = false;
+  *count = k;
+  return FOA_DMD_OK;
+}

@@ -9,7 +9,8 @@ namespace foa {
 // Launch-geometry knobs of the streaming passes (set per handle; the autotuner may change them).
 struct Geometry {
   int64_t stage_bytes = 32 * 1024;     // target bytes of V per pipeline stage
-  int64_t smem_budget = 200 * 1024;    // shared memory one CTA may use
+  int64_t smem_budget = 200 * 1024;    // shared memory of a CTA when one CTA runs per SM
+  int64_t smem_budget2 = 112 * 1024;   // ... when two CTAs share an SM
   int64_t inflight_bytes = 96 * 1024;  // bytes of V each CTA keeps in flight
   int max_ctas_per_sm = 2;
 };
@@ -54,6 +55,14 @@ struct foa_dmd {
   size_t prof_used = 0;
   std::vector<foa::EventPair> events;
   foa::EigWork *eig = nullptr;
+  // push-time indicator (side stream)
+  foa::EigWork *ind_eig = nullptr;
+  cudaStream_t ind_stream = nullptr;
+  cudaEvent_t ind_event = nullptr;
+  void *ind_ring = nullptr;
+  int64_t ind_issued = 0, ind_read = 0;
+  bool ind_pending = false;
+  bool ind_this_push = false;  // the most recent push scheduled an indicator
 };
 
 namespace foa {
@@ -70,4 +79,6 @@ int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_
 // eigen path (eig.cu)
 void eig_free(foa_dmd *h);
 int maybe_indicator(foa_dmd *h);  // the indicator schedule of foa_dmd_opts.indicator_every
+double latest_indicator(foa_dmd *h, bool only_if_pending);
+constexpr int kIndRing = 1024;
 }  // namespace foa

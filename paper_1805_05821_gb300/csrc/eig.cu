@@ -519,6 +519,7 @@ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
 __global__ void vectors_kernel(EigArgs e) {
   const int r = e.isc[ISC_R];
   const int m = e.m;
+  const double hlast = *e.hlast_p, b11 = *e.b11_p;
   extern __shared__ double sh[];
   double *cr = sh, *ci = sh + r;                 // current LU row / work vector
   double *br = sh + 2 * r, *bi = sh + 3 * r;     // right-hand side / solution
@@ -721,7 +722,7 @@ __global__ void vectors_kernel(EigArgs e) {
     // ---- amplitude c = (w^H b) / (w^H z), b = beta_11 U_r^T e_1
     double n1r = 0.0, n1i = 0.0, d1r = 0.0, d1i = 0.0;
     for (int c = threadIdx.x; c < r; c += blockDim.x) {
-      const double bc = e.b11 * (e.have_u ? e.U[0 + int64_t(c) * e.ld] : (c == 0 ? 1.0 : 0.0));
+      const double bc = b11 * (e.have_u ? e.U[0 + int64_t(c) * e.ld] : (c == 0 ? 1.0 : 0.0));
       // conj(w) * b
       n1r += wr_s[c] * bc;
       n1i += -wi_s[c] * bc;
@@ -756,7 +757,7 @@ __global__ void vectors_kernel(EigArgs e) {
     double ind;
     if (!e.have_u) {
       const double zl2 = zr_s[m - 1] * zr_s[m - 1] + zi_s[m - 1] * zi_s[m - 1];
-      ind = fabs(e.hlast) * sqrt(zl2);
+      ind = fabs(hlast) * sqrt(zl2);
     } else {
       // t = H_m y; t <- t - U_r (U_r^T t); ind = sqrt(|t|^2 + |h y_m|^2)
       double *tr = e.tw + size_t(blockIdx.x) * 2 * size_t(e.ld), *ti = tr + e.ld;
@@ -794,7 +795,7 @@ __global__ void vectors_kernel(EigArgs e) {
         acc += sr * sr + si * si;
       }
       acc = block_sum(acc, red);
-      const double hy2 = e.hlast * e.hlast * (yr[m - 1] * yr[m - 1] + yi[m - 1] * yi[m - 1]);
+      const double hy2 = hlast * hlast * (yr[m - 1] * yr[m - 1] + yi[m - 1] * yi[m - 1]);
       ind = sqrt(acc + hy2);
     }
     if (threadIdx.x == 0) {

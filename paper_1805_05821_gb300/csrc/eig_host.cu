@@ -11,23 +11,33 @@ namespace foa {
 
 static constexpr int kVecGridMax = 64;  // CTAs of the inverse-iteration kernel (each owns LU scratch)
 
-void eig_free(foa_dmd *h) {
-  EigWork *w = h->eig;
-  if (!w) return;
+static void free_work(EigWork *w) {
   void *ptrs[] = {w->A,  w->U,  w->sig_raw, w->sig, w->G,      w->Q,     w->T,     w->Aqr,   w->wr,
                   w->wi, w->yr, w->yi,      w->ysr, w->ysi,    w->ind,   w->amp_re, w->amp_im, w->out,
-                  w->anorm, w->lu, w->tw, w->yplanes, w->perm, w->isc, w->gb};
+                  w->anorm, w->lu, w->tw, w->yplanes, w->perm, w->isc, w->gb, w->bop};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;
-  h->eig = nullptr;
 }
 
-static int eig_alloc(foa_dmd *h) {
-  if (h->eig) return FOA_DMD_OK;
+void eig_free(foa_dmd *h) {
+  if (h->ind_stream) cudaStreamSynchronize(h->ind_stream);
+  if (h->eig) free_work(h->eig);
+  if (h->ind_eig) free_work(h->ind_eig);
+  h->eig = h->ind_eig = nullptr;
+  if (h->ind_ring) cudaFree(h->ind_ring);
+  h->ind_ring = nullptr;
+  if (h->ind_event) cudaEventDestroy(h->ind_event);
+  h->ind_event = nullptr;
+  if (h->ind_stream) cudaStreamDestroy(h->ind_stream);
+  h->ind_stream = nullptr;
+}
+
+static int eig_alloc(foa_dmd *h, EigWork **slot) {
+  if (*slot) return FOA_DMD_OK;
   EigWork *w = new (std::nothrow) EigWork();
   if (!w) return FOA_DMD_ENOMEM;
-  h->eig = w;
+  *slot = w;
   const int K = h->kmax;
   w->K = K;
   w->vgrid = kVecGridMax;
@@ -42,11 +52,13 @@ static int eig_alloc(foa_dmd *h) {
   AL(w->ind, K1); AL(w->amp_re, K1); AL(w->amp_im, K1); AL(w->out, OUT_N * K1); AL(w->anorm, 8);
   AL(w->lu, size_t(w->vgrid) * 2 * K2); AL(w->tw, size_t(w->vgrid) * 2 * K1); AL(w->yplanes, 2 * K2);
   AL(w->perm, size_t(K) * 4); AL(w->isc, ISC_N * 4); AL(w->gb, sizeof(GridBar));
+  AL(w->bop, modes_tc_bop_bytes(K));
 #undef AL
   if (e == cudaSuccess) e = cudaMemset(w->gb, 0, sizeof(GridBar));
   if (e == cudaSuccess) e = cudaMemset(w->isc, 0, ISC_N * 4);
   if (e != cudaSuccess) {
-    eig_free(h);
+    free_work(w);
+    *slot = nullptr;
     return cuda_status(e);
   }
   return FOA_DMD_OK;
@@ -63,39 +75,21 @@ struct EigOut {
   std::vector<double> out;  // OUT_N x K
 };
 
-// Run the eigen path up to the sorted scalars and y columns (device); copies the scalars back.
-static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
-  int rc = sync_state(h, nullptr);
-  if (rc) return rc;
-  const int q = h->q_host;
-  const int m = h->stopped_host ? q : q - 1;
-  if (m < 1) return FOA_DMD_EINVAL;
-  rc = eig_alloc(h);
-  if (rc) return rc;
-  EigWork *w = h->eig;
+// Enqueue the eigen path on stream s with workspace w for the projected matrix of size m: all
+// launch sizes are bounded by m and the truncated rank r is read on the device, so nothing here
+// waits for the GPU.  rank_tol as for foa_dmd_eig.
+static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double rank_tol, int nsel) {
   const int K = h->kmax;
-  cudaStream_t s = h->stream;
-  double hb[2];
-  cudaError_t e = cudaMemcpyAsync(&hb[0], h->H + m + int64_t(m - 1) * K, 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb[1], h->B, 8, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(w->isc, 0, ISC_N * 4, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaError_t e = cudaMemsetAsync(w->isc, 0, ISC_N * 4, s);
   if (e != cudaSuccess) return cuda_status(e);
-  const double hlast = (m < K) ? hb[0] : 0.0;
-  const double b11 = hb[1];
   double tol = 0.0;
   if (rank_tol > 0.0) tol = rank_tol;
   else if (rank_tol < 0.0) tol = (m + 1) * eps_of(h->dtype);
   const bool trunc = tol > 0.0;
-  int r = m;
   if (trunc) {
-    // cooperative one-sided Jacobi SVD of beta_m
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, svd_jacobi_kernel, 256, 0);
-    if (e != cudaSuccess) return cuda_status(e);
-    int grid = h->sms * (per_sm < 1 ? 1 : (per_sm > 1 ? 1 : per_sm));
-    const int need = ((m + 1) / 2 + 7) / 8;  // one warp per pair
-    if (grid > need) grid = need;
+    // cooperative one-sided Jacobi SVD of beta_m (one warp per column pair)
+    int grid = ((m + 1) / 2 + 7) / 8;
+    if (grid > h->sms) grid = h->sms;
     if (grid < 1) grid = 1;
     const double *Bp = h->B;
     int ldb = K, mm = m, lda = K, sweeps = 30, *iscp = w->isc;
@@ -105,15 +99,9 @@ static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
     e = cudaLaunchCooperativeKernel((void *)svd_jacobi_kernel, grid, 256, args, 0, s);
     if (e != cudaSuccess) return cuda_status(e);
     svd_finish_kernel<<<1, 512, size_t(m) * 12 + 64, s>>>(w->A, K, m, w->sig_raw, w->U, w->sig, w->isc, tol);
-    int iscv[ISC_N];
-    e = cudaMemcpyAsync(iscv, w->isc, sizeof(iscv), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e);
-    if (iscv[ISC_ERR]) return iscv[ISC_ERR];
-    r = iscv[ISC_R];
     project_t_kernel<<<h->sms * 2, 256, 0, s>>>(h->H, K, m, w->U, K, w->isc, w->T, K);
     project_g_kernel<<<h->sms * 2, 256, 0, s>>>(w->U, K, m, w->isc, w->T, K, w->G, K);
-    hessenberg_kernel<<<1, 512, size_t(r) * 8 + 32 * 8, s>>>(w->G, K, w->Q, K, w->isc);
+    hessenberg_kernel<<<1, 512, size_t(m) * 8 + 32 * 8, s>>>(w->G, K, w->Q, K, w->isc);
     h->launches += 5;
   } else {
     copy_h_kernel<<<h->sms, 256, 0, s>>>(h->H, K, m, w->G, K, w->isc);
@@ -122,7 +110,7 @@ static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
   anorm_kernel<<<1, 512, 0, s>>>(w->G, K, w->isc, w->anorm);
   e = cudaMemcpyAsync(w->Aqr, w->G, size_t(K) * K * 8, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  const size_t qr_smem = size_t(r) * r * 8;
+  const size_t qr_smem = size_t(m) * m * 8;
   const bool use_smem = qr_smem <= 200 * 1024;
   if (use_smem && qr_smem > 48 * 1024) {
     e = cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
@@ -155,28 +143,59 @@ static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
   a.m = m;
   a.have_q = trunc ? 1 : 0;
   a.have_u = trunc ? 1 : 0;
-  a.hlast = hlast;
-  a.b11 = b11;
-  const int vgrid = r < w->vgrid ? r : w->vgrid;
-  const size_t vsmem = (size_t(r) * 10 + size_t(r + 1) / 2 + 64) * 8;
+  a.hlast_p = h->H + m + int64_t(m - 1) * K;  // h_{m+1,m} (0 after a breakdown)
+  a.b11_p = h->B;
+  const int vgrid = m < w->vgrid ? m : w->vgrid;
+  const size_t vsmem = (size_t(m) * 10 + size_t(m + 1) / 2 + 64) * 8;
   vectors_kernel<<<vgrid, 256, vsmem, s>>>(a);
-  if (nsel > r) nsel = r;
-  order_kernel<<<1, 512, size_t(r) * 20 + 64, s>>>(a, nsel);
+  if (nsel > m) nsel = m;
+  order_kernel<<<1, 512, size_t(m) * 20 + 64, s>>>(a, nsel);
   h->launches += 4;  // anorm, hqr, vectors, order
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_status(e);
+  return cuda_status(cudaGetLastError());
+}
+
+// Synchronous eigen path on the handle's stream; copies the sorted scalars back.
+static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
+  int rc = sync_state(h, nullptr);
+  if (rc) return rc;
+  const int q = h->q_host;
+  const int m = h->stopped_host ? q : q - 1;
+  if (m < 1) return FOA_DMD_EINVAL;
+  rc = eig_alloc(h, &h->eig);
+  if (rc) return rc;
+  EigWork *w = h->eig;
+  const int K = h->kmax;
+  cudaStream_t s = h->stream;
+  rc = enqueue_eig(h, w, s, m, rank_tol, nsel);
+  if (rc) return rc;
   res.out.resize(size_t(OUT_N) * K);
   int iscv[ISC_N];
-  e = cudaMemcpyAsync(res.out.data(), w->out, res.out.size() * 8, cudaMemcpyDeviceToHost, s);
+  double hb = 0.0;
+  cudaError_t e = cudaMemcpyAsync(res.out.data(), w->out, res.out.size() * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(iscv, w->isc, sizeof(iscv), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, h->H + m + int64_t(m - 1) * K, 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
   if (iscv[ISC_ERR]) return iscv[ISC_ERR];
   res.m = m;
-  res.r = r;
-  res.hlast = hlast;
+  res.r = iscv[ISC_R];
+  res.hlast = hb;
   res.status = iscv[ISC_STATUS];
   return res.status;
+}
+
+// max of the error indicators of the n_lead leading modes into the indicator ring
+__global__ void ind_record_kernel(const double *out, int ld, const int *isc, int n_lead, IndRecord *rec, int push,
+                                  int m) {
+  if (threadIdx.x != 0) return;
+  const int r = isc[ISC_R];
+  const int nl = r < n_lead ? r : n_lead;
+  double v = 0.0;
+  for (int i = 0; i < nl; ++i) v = fmax(v, out[OUT_IND * ld + i]);
+  if (isc[ISC_STATUS] != FOA_DMD_OK || isc[ISC_ERR] != 0) v = __longlong_as_double(0x7ff8000000000000ll);
+  rec->push = push;
+  rec->m = m;
+  rec->value = v;
 }
 
 // interleave the sorted y columns into real planes [Re y_0, Im y_0, Re y_1, ...] (m x 2 ncols)
@@ -189,21 +208,54 @@ __global__ void planes_kernel(const double *ysr, const double *ysi, int ld, int 
   }
 }
 
+// The indicator schedule: every indicator_every-th push enqueues the eigen path for the projected
+// matrix of that moment on a low-priority side stream (its own workspace), after the push's
+// passes.  H-bar's leading m columns never change once written, so the eigensolve overlaps the
+// following pushes; the streaming passes leave one SM free for it.  Results go to a device ring
+// read by foa_dmd_indicators (and by a push that asks for its info).
 int maybe_indicator(foa_dmd *h) {
   h->pushes_host += 1;
+  h->ind_this_push = false;
   const int every = h->opts.indicator_every;
   if (every <= 0 || h->pushes_host % every != 0) return FOA_DMD_OK;
-  EigOut res;
-  int rc = run_eig(h, h->opts.indicator_rank_tol, 0, res);
-  if (rc == FOA_DMD_EINVAL) return FOA_DMD_OK;  // fewer than two snapshots: nothing to indicate
+  const int m = h->stopped_host ? h->q_host : h->q_host - 1;
+  if (m < 1) return FOA_DMD_OK;
+  cudaError_t e = cudaSuccess;
+  if (!h->ind_stream) {
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->ind_stream, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ind_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&h->ind_ring, sizeof(IndRecord) * kIndRing);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int rc = eig_alloc(h, &h->ind_eig);
   if (rc) return rc;
-  const int K = h->kmax;
-  const int nl = res.r < h->opts.n_lead ? res.r : h->opts.n_lead;
-  double ind = 0.0;
-  for (int i = 0; i < nl; ++i) ind = std::fmax(ind, res.out[size_t(OUT_IND) * K + i]);
-  cudaError_t e = cudaMemcpyAsync(&h->st->info.indicator, &ind, 8, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  return cuda_status(e);
+  e = cudaEventRecord(h->ind_event, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->ind_stream, h->ind_event, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  rc = enqueue_eig(h, h->ind_eig, h->ind_stream, m, h->opts.indicator_rank_tol, 0);
+  if (rc) return rc;
+  IndRecord *rec = static_cast<IndRecord *>(h->ind_ring) + (h->ind_issued % kIndRing);
+  ind_record_kernel<<<1, 32, 0, h->ind_stream>>>(h->ind_eig->out, h->kmax, h->ind_eig->isc, h->opts.n_lead, rec,
+                                                 h->pushes_host, m);
+  h->launches += 1;
+  h->ind_issued += 1;
+  h->ind_pending = true;
+  h->ind_this_push = true;
+  return cuda_status(cudaGetLastError());
+}
+
+// Latest indicator value (synchronises the side stream); NaN when none was scheduled.
+double latest_indicator(foa_dmd *h, bool only_if_pending) {
+  if (!h->ind_stream || h->ind_issued == 0 || (only_if_pending && !h->ind_pending)) return NAN;
+  IndRecord r;
+  cudaError_t e = cudaStreamSynchronize(h->ind_stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&r, static_cast<IndRecord *>(h->ind_ring) + ((h->ind_issued - 1) % kIndRing), sizeof(r),
+                   cudaMemcpyDeviceToHost);
+  h->ind_pending = false;
+  return e == cudaSuccess ? r.value : NAN;
 }
 
 }  // namespace foa
@@ -259,8 +311,11 @@ extern "C" int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *re
     h->launches += 2;  // planes and the modes GEMM
     rc = launch_modes(h, o.m, w->yplanes, K, 2 * nm, res->phi_dev, res->ld_phi);
     if (rc) return rc;
-    e = cudaStreamSynchronize(h->stream);
+    int errv = 0;
+    e = cudaMemcpyAsync(&errv, w->isc + ISC_ERR, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
+    if (errv) return errv;
   }
   return FOA_DMD_OK;
 }

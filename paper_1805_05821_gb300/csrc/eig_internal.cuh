@@ -31,7 +31,15 @@ struct EigArgs {
   int *isc;
   int ld, m;
   int have_q, have_u;
-  double hlast, b11;
+  const double *hlast_p;  // h_{m+1,m} (device)
+  const double *b11_p;    // beta_{1,1} (device)
+};
+
+// one push-time indicator (device ring written by the indicator stream)
+struct IndRecord {
+  int32_t push;   // 1-based index of the push that scheduled it
+  int32_t m;      // size of the projected matrix
+  double value;   // max over the n_lead leading modes
 };
 
 struct EigWork {
@@ -41,6 +49,7 @@ struct EigWork {
          *Aqr = nullptr, *wr = nullptr, *wi = nullptr, *yr = nullptr, *yi = nullptr, *ysr = nullptr, *ysi = nullptr,
          *ind = nullptr, *amp_re = nullptr, *amp_im = nullptr, *out = nullptr, *anorm = nullptr, *lu = nullptr,
          *tw = nullptr, *yplanes = nullptr;
+  float *bop = nullptr;  // pre-split Y operand of the tensor-core mode product
   int *perm = nullptr, *isc = nullptr;
   GridBar *gb = nullptr;
 };
@@ -60,6 +69,7 @@ __global__ void vectors_kernel(EigArgs e);
 __global__ void order_kernel(EigArgs e, int nsel);
 __global__ void anorm_kernel(const double *Hs, int ld, const int *isc, double *out);
 
+size_t modes_tc_bop_bytes(int kmax);
 // modes.cu: Phi = V Y (Y: m x ncols real planes, ld), written to phi (ld_phi)
 int launch_modes(foa_dmd *h, int m, const double *Y, int ldy, int ncols, void *phi, int64_t ld_phi);
 

@@ -1,6 +1,8 @@
 // DMD modes Phi_i = V_{1:m} U_r z_i (Alg. 1 step 26): Phi = V Y with Y = [Re y_0, Im y_0, ...]
 // (m x ncols, FP64).  SIMT form: each CTA stages 32-row tiles of the row-tiled V in shared
 // memory and every thread accumulates ncols/8 outputs of one row.
+#include <cstdlib>
+
 #include "api_internal.cuh"
 #include "eig_internal.cuh"
 
@@ -45,8 +47,16 @@ __global__ void __launch_bounds__(256) modes_simt_kernel(const S *V, int kmax, i
   }
 }
 
+int launch_modes_tc(foa_dmd *h, int m, const double *Y, int ldy, int ncols, float *phi, int64_t ld_phi, float *Bop,
+                    int *err);
+
 int launch_modes(foa_dmd *h, int m, const double *Y, int ldy, int ncols, void *phi, int64_t ld_phi) {
   if (ncols > 64) return FOA_DMD_EINVAL;
+  // FP32 storage: tensor cores (tcgen05, kind::tf32 with a three-term split).  FOA_DMD_MODES_SIMT=1
+  // selects the SIMT kernel instead (used by the tests as an independent cross-check).
+  const char *simt = getenv("FOA_DMD_MODES_SIMT");
+  if (h->dtype == FOA_DMD_F32 && !(simt && simt[0] == '1'))
+    return launch_modes_tc(h, m, Y, ldy, ncols, static_cast<float *>(phi), ld_phi, h->eig->bop, h->eig->isc + ISC_ERR);
   const int cs = compute_size(h->dtype), s = dtype_size(h->dtype);
   const size_t smem = ((size_t(m) * ncols * cs + 15) / 16) * 16 + size_t(kTile) * m * s;
   if (smem > 232448) return FOA_DMD_EINVAL;

@@ -29,8 +29,15 @@
 
 namespace foa {
 
+// Two CTAs per SM for the FP32/BF16 forms while the column accumulators fit (NC <= 48, i.e.
+// j <= 384): one CTA's barrier phases then overlap the other's compute.
+template <typename S, int NC>
+constexpr int pass_min_blocks() {
+  return (sizeof(typename Compute<S>::T) == 4 && NC <= 48) ? 2 : 1;
+}
+
 template <typename S, int MODE, int NC>
-__global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kernel(const PassArgs a) {
   using C = typename Compute<S>::T;
   constexpr bool kFp64 = sizeof(C) == 8;
   constexpr bool kDots = (MODE == PASS_A || MODE == PASS_B);
@@ -113,9 +120,18 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
   C acc[kDots ? NC : 1];
 #pragma unroll
   for (int k = 0; k < (kDots ? NC : 1); ++k) acc[k] = C(0);
-  double nacc = 0.0;
+  // sum of squares for the norms: compensated (Kahan) in the compute type per thread, folded into
+  // FP64 once at the end
+  C nsum = C(0), ncomp = C(0);
+  auto nrm_add = [&](C v) {
+    const C y = v - ncomp;
+    const C t = nsum + y;
+    ncomp = (t - nsum) - y;
+    nsum = t;
+  };
   int since_flush = 0;
   int it = 0;
+  int prev_slot = -1;
   bool aborted = false;
 
   auto flush = [&]() {
@@ -141,6 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
       if (tid == 0) atomicExch(&st->err, FOA_DMD_ETIMEOUT);
       break;
     }
+    if (prev_slot >= 0 && tid == 0) mbar_arrive(&empty[prev_slot]);
     const int t0 = s * a.R;
     const int nt = min(a.R, a.ntiles - t0);
     const int RS = nt * kTile;
@@ -154,8 +171,6 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
     // ---------------- sweep 1: row-local part
     const int G = (RS >= kConsumers || j == 0) ? 1 : (kConsumers / RS);
     const int active_rows_threads = (G == 1) ? kConsumers : G * RS;
-    float nstage_f = 0.f;
-    double nstage_d = 0.0;
     if (tid < active_rows_threads) {
       const int g = (G == 1) ? 0 : tid / RS;
       const int cpg = (j + G - 1) / G;
@@ -164,6 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
       for (int row = (G == 1 ? tid : tid % RS); row < RS; row += (G == 1 ? kConsumers : RS)) {
         const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
         double accd = 0.0;
+        float accf = 0.f;
         if constexpr (kFp64) {
           double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
           int c = c0;
@@ -176,42 +192,42 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
           for (; c < c1; ++c) b0 = fma(to_c(vr[c * kTile]), cf[c], b0);
           accd = (b0 + b1) + (b2 + b3);
         } else {
-          for (int cb = c0; cb < c1; cb += 32) {
-            const int ce = min(c1, cb + 32);
-            float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
-            int c = cb;
-            for (; c + 4 <= ce; c += 4) {
-              b0 = fmaf(to_c(vr[(c + 0) * kTile]), cf[c + 0], b0);
-              b1 = fmaf(to_c(vr[(c + 1) * kTile]), cf[c + 1], b1);
-              b2 = fmaf(to_c(vr[(c + 2) * kTile]), cf[c + 2], b2);
-              b3 = fmaf(to_c(vr[(c + 3) * kTile]), cf[c + 3], b3);
-            }
-            for (; c < ce; ++c) b0 = fmaf(to_c(vr[c * kTile]), cf[c], b0);
-            accd += static_cast<double>((b0 + b1) + (b2 + b3));
+          // FP32: four independent chains over the thread's columns (no FP64 in the row loop:
+          // the FP64 pipe of this part is ~1/64 of FP32)
+          float b[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) b[u] = 0.f;
+          int c = c0;
+          for (; c + 8 <= c1; c += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = to_c(vr[(c + u) * kTile]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) b[u] = fmaf(v[u], cf[c + u], b[u]);
           }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (c + u < c1) b[u] = fmaf(to_c(vr[(c + u) * kTile]), cf[c + u], b[u]);
+          accf = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
         }
         if (G > 1) {
-          comb[g * RS + row] = accd;
+          if constexpr (kFp64) comb[g * RS + row] = accd;
+          else reinterpret_cast<float *>(comb)[g * RS + row] = accf;
         } else {
           // finish the row here
           const int64_t r = r0 + row;
-          double base;
-          if (base_bulk) base = static_cast<double>(to_c(bs[row]));
-          else base = (r < a.n) ? static_cast<double>(to_c(bg[r])) : 0.0;
+          C base;
+          if (base_bulk) base = to_c(bs[row]);
+          else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
           if constexpr (MODE == PASS_FIRST) {
-            const C xv = static_cast<C>(base);
-            if constexpr (kFp64) nstage_d += double(xv) * double(xv); else nstage_f = fmaf(xv, xv, nstage_f);
+            nrm_add(base * base);
           } else {
-            const double wnew = (MODE == PASS_A) ? (base - accd) * cscale : (base - accd);
-            const C wc = static_cast<C>(wnew);
+            const C acc = kFp64 ? C(accd) : C(accf);
+            const C wc = (MODE == PASS_A) ? (base - acc) * C(cscale) : (base - acc);
             static_cast<C *>(a.w)[r] = wc;
             ws[row] = wc;
-            if constexpr (MODE == PASS_A) {
-              const C xv = static_cast<C>(base);
-              if constexpr (kFp64) nstage_d += double(xv) * double(xv); else nstage_f = fmaf(xv, xv, nstage_f);
-            } else if constexpr (MODE == PASS_C) {
-              if constexpr (kFp64) nstage_d += double(wc) * double(wc); else nstage_f = fmaf(wc, wc, nstage_f);
-            }
+            if constexpr (MODE == PASS_A) nrm_add(base * base);
+            else if constexpr (MODE == PASS_C) nrm_add(wc * wc);
           }
         }
       }
@@ -220,25 +236,24 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
       named_bar_sync(1, kConsumers);
       if (tid < RS) {
         const int row = tid;
-        double accd = 0.0;
-        for (int g = 0; g < G; ++g) accd += comb[g * RS + row];
+        C acc = C(0);
+        if constexpr (kFp64) {
+          for (int g = 0; g < G; ++g) acc += comb[g * RS + row];
+        } else {
+          const float *cb = reinterpret_cast<const float *>(comb);
+          for (int g = 0; g < G; ++g) acc += cb[g * RS + row];
+        }
         const int64_t r = r0 + row;
-        double base;
-        if (base_bulk) base = static_cast<double>(to_c(bs[row]));
-        else base = (r < a.n) ? static_cast<double>(to_c(bg[r])) : 0.0;
-        const double wnew = (MODE == PASS_A) ? (base - accd) * cscale : (base - accd);
-        const C wc = static_cast<C>(wnew);
+        C base;
+        if (base_bulk) base = to_c(bs[row]);
+        else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
+        const C wc = (MODE == PASS_A) ? (base - acc) * C(cscale) : (base - acc);
         static_cast<C *>(a.w)[r] = wc;
         ws[row] = wc;
-        if constexpr (MODE == PASS_A) {
-          const C xv = static_cast<C>(base);
-          if constexpr (kFp64) nstage_d += double(xv) * double(xv); else nstage_f = fmaf(xv, xv, nstage_f);
-        } else if constexpr (MODE == PASS_C) {
-          if constexpr (kFp64) nstage_d += double(wc) * double(wc); else nstage_f = fmaf(wc, wc, nstage_f);
-        }
+        if constexpr (MODE == PASS_A) nrm_add(base * base);
+        else if constexpr (MODE == PASS_C) nrm_add(wc * wc);
       }
     }
-    if constexpr (kNorm) nacc += kFp64 ? nstage_d : static_cast<double>(nstage_f);
     named_bar_sync(1, kConsumers);  // ws complete
 
     // ---------------- sweep 2: column dot products over the staged rows
@@ -263,8 +278,12 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
         }
       }
     }
-    named_bar_sync(1, kConsumers);  // slot and ws free
-    if (tid == 0) mbar_arrive(&empty[slot]);
+    // the slot is released after the next stage's vote barrier (all consumers are past sweep 2)
+    prev_slot = slot;
+  }
+  if (prev_slot >= 0 && !aborted) {
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) mbar_arrive(&empty[prev_slot]);
   }
 
   if (aborted) {
@@ -276,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, 1) pass_kernel(const PassArgs a) {
     return;
   }
   flush();
-  if constexpr (kNorm) nrm[tid] = nacc;
+  if constexpr (kNorm) nrm[tid] = double(nsum) - double(ncomp);
   named_bar_sync(1, kConsumers);
   const int len = j + 1;
   if (tid == 0) {

@@ -22,6 +22,7 @@ static cudaError_t launch_nc(int nc, const PassArgs &a, int grid, cudaStream_t s
     case 8: return launch_one<MODE, 8>(a, grid, s);
     case 16: return launch_one<MODE, 16>(a, grid, s);
     case 32: return launch_one<MODE, 32>(a, grid, s);
+    case 48: return launch_one<MODE, 48>(a, grid, s);
     default: return launch_one<MODE, 64>(a, grid, s);
   }
 }

@@ -19,7 +19,7 @@ cudaError_t launch_pass(int dtype, int mode, int nc, const PassArgs &a, int grid
 
 int pass_nc_for(int jcap) {
   const int need = (jcap + kWarps - 1) / kWarps;
-  return need <= 8 ? 8 : need <= 16 ? 16 : need <= 32 ? 32 : 64;
+  return need <= 8 ? 8 : need <= 16 ? 16 : need <= 32 ? 32 : need <= 48 ? 48 : 64;
 }
 
 // Decide whether the push proceeds and compute beta_pre (Alg. 1 steps 5-8):

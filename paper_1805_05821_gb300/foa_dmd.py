@@ -71,6 +71,8 @@ def lib():
             "foa_dmd_push_batch": (ctypes.c_int, [vp, vp, i32, i64, ctypes.POINTER(foa_dmd_push_info)]),
             "foa_dmd_push_host": (ctypes.c_int, [vp, vp, ctypes.POINTER(foa_dmd_push_info)]),
             "foa_dmd_sync": (ctypes.c_int, [vp, ctypes.POINTER(foa_dmd_push_info)]),
+            "foa_dmd_indicators": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), _DP, i32,
+                                                  ctypes.POINTER(i32)]),
             "foa_dmd_eig": (ctypes.c_int, [vp, d, ctypes.POINTER(foa_dmd_eig_result)]),
             "foa_dmd_get_state": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), _DP, _DP, i32]),
             "foa_dmd_get_basis": (ctypes.c_int, [vp, i32, i32, vp, i64]),
@@ -162,6 +164,16 @@ def foa_dmd_sync(h):
     info = foa_dmd_push_info()
     st = lib().foa_dmd_sync(h, ctypes.byref(info))
     return st, info
+
+
+def foa_dmd_indicators(h, cap=1024):
+    pi = (ctypes.c_int32 * cap)()
+    mm = (ctypes.c_int32 * cap)()
+    val = np.zeros(cap)
+    cnt = ctypes.c_int32()
+    _check(lib().foa_dmd_indicators(h, pi, mm, val.ctypes.data_as(_DP), cap, ctypes.byref(cnt)), "foa_dmd_indicators")
+    k = cnt.value
+    return [(int(pi[i]), int(mm[i]), float(val[i])) for i in range(k)]
 
 
 def foa_dmd_get_state(h, k_max):
@@ -331,6 +343,9 @@ class FoaDMD:
     def sync(self):
         st, inf = foa_dmd_sync(self.h)
         return st, inf.as_dict()
+
+    def indicators(self):
+        return foa_dmd_indicators(self.h)
 
     def state(self):
         return foa_dmd_get_state(self.h, self.k_max)

@@ -1,0 +1,128 @@
+"""Batched streams (one persistent launch per push of every stream) against the FP64 oracle.
+
+Streams of uneven n and k_max, FP32 storage, planted maps with noise (the batched workload's
+recipe at small sizes); some streams sit out some pushes.  Each stream's beta and H-bar must
+match an oracle run on the same rounded inputs within k_max u_fp32 kappa_2(X).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from gpu_util import U, kappa_of, rel, to_device
+from paper_1805_05821_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1805_05821_gb300 import build
+    build.build()
+
+
+def make_streams():
+    rng = np.random.default_rng(3)
+    out = []
+    for s in range(6):
+        n = int(rng.integers(500, 70000))
+        N = int(rng.integers(10, 40))
+        out.append(synth.planted(n, N, int(rng.integers(6, 12)) * 2, seed=100 + s, noise_rel=1e-5))
+    return out
+
+
+def oracle_state(Xr, k):
+    import oracle
+    o = oracle.FoaOracle(Xr.shape[0], k, storage="f32")
+    for t in range(Xr.shape[1]):
+        if o.push(Xr[:, t])[0] != "ok":
+            break
+    return o
+
+
+def run_batch(specs, skip, use_graph=False):
+    import torch
+    from paper_1805_05821_gb300 import foa_dmd as F
+    S = len(specs)
+    devs, hosts = [], []
+    for sp in specs:
+        Xr, Xd = to_device(synth.snapshots(sp), "f32")
+        hosts.append(Xr)
+        devs.append(Xd)
+    stream = torch.cuda.Stream()
+    opts = F.foa_dmd_opts_default()
+    opts.cuda_stream = stream.cuda_stream
+    b = F.foa_dmd_batch_create([sp.n for sp in specs], [sp.N for sp in specs], "f32", opts)
+    ptrs = torch.zeros(S, dtype=torch.int64, device="cuda")
+    hl = torch.zeros(S, dtype=torch.float64, device="cuda")
+    T = max(sp.N for sp in specs) + 3
+    pushed = [0] * S
+    graph = None
+    if use_graph:
+        graph = torch.cuda.CUDAGraph()
+    for r in range(T):
+        host_ptrs = []
+        for s, sp in enumerate(specs):
+            if pushed[s] < sp.N and (r, s) not in skip:
+                host_ptrs.append(int(devs[s][pushed[s]].data_ptr()))
+                pushed[s] += 1
+            else:
+                host_ptrs.append(0)
+        with torch.cuda.stream(stream):
+            ptrs.copy_(torch.tensor(host_ptrs, dtype=torch.int64), non_blocking=False)
+            if use_graph:
+                if r == 0:
+                    with torch.cuda.graph(graph, stream=stream):
+                        rc = F.foa_dmd_batch_push(b, ptrs, hl)
+                    assert rc == 0
+                graph.replay()
+            else:
+                assert F.foa_dmd_batch_push(b, ptrs, hl) == 0
+        stream.synchronize()
+    return b, hosts
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_streams_match_oracle(use_graph):
+    from paper_1805_05821_gb300 import foa_dmd as F
+    specs = make_streams()
+    skip = {(3, 1), (4, 1), (7, 4), (0, 5)}
+    b, hosts = run_batch(specs, skip, use_graph)
+    try:
+        for s, sp in enumerate(specs):
+            q, status, H, B = F.foa_dmd_batch_get_state(b, s, sp.N)
+            o = oracle_state(hosts[s], sp.N)
+            assert q == o.q, (s, q, o.q)
+            kap = kappa_of(o.B, q)
+            tol = sp.N * U["f32"] * kap
+            assert rel(B[:q, :q], o.B[:q, :q]) <= tol, s
+            m = o.m
+            assert rel(H[:m + 1, :m], o.H[:m + 1, :m]) <= tol, s
+    finally:
+        F.foa_dmd_batch_destroy(b)
+
+
+def test_batched_equals_single_stream_structure():
+    """The same stream pushed alone (single-stream API) and inside a batch gives the same q and
+    agrees to rounding (different summation orders)."""
+    import torch
+    from paper_1805_05821_gb300 import foa_dmd as F
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    sp = synth.planted(40000, 30, 16, seed=5, noise_rel=1e-5)
+    Xr, Xd = to_device(synth.snapshots(sp), "f32")
+    g = FoaDMD(sp.n, 30, "f32", breakdown_tol=1e-9)
+    for t in range(30):
+        assert g.push(Xd[t], info=False)[0] == 0
+    opts = F.foa_dmd_opts_default()
+    opts.breakdown_tol = 1e-9
+    b = F.foa_dmd_batch_create([sp.n], [30], "f32", opts)
+    ptrs = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for t in range(30):
+        ptrs.fill_(int(Xd[t].data_ptr()))
+        assert F.foa_dmd_batch_push(b, ptrs, None) == 0
+    torch.cuda.synchronize()
+    q1, _, H1, B1 = g.state()
+    q2, st, H2, B2 = F.foa_dmd_batch_get_state(b, 0, 30)
+    F.foa_dmd_batch_destroy(b)
+    assert q1 == q2 == 30
+    assert rel(B2, B1) <= 1e-5 and rel(H2[:30, :29], H1[:30, :29]) <= 1e-4

@@ -143,3 +143,52 @@ def test_indicator_schedule():
             assert abs(inf["indicator"] - want) <= 1e-7 * want + 1e-14, (t, inf["indicator"], want)
         else:
             assert np.isnan(inf["indicator"])
+
+
+def test_tensor_core_modes_match_simt_and_oracle(monkeypatch):
+    """Phi = V Y on tcgen05 (three-term TF32 split) against the SIMT FP32 kernel and the oracle,
+    with a ragged n (not a multiple of the 256-row block) and m not a multiple of 16."""
+    spec = synth.waves(40, 2, 1, 27, 12, 7, noise_rel=1e-6)  # n = 1600, N = 27 -> m = 26
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f32")
+    g, _ = run_gpu(Xd, spec.n, 27, "f32")
+    o, _ = run_oracle(Xr, 27, "f32")
+    monkeypatch.setenv("FOA_DMD_MODES_SIMT", "0")
+    rt = g.eig(0.0, n_modes=32, vec_cols=26)
+    monkeypatch.setenv("FOA_DMD_MODES_SIMT", "1")
+    rs = g.eig(0.0, n_modes=32)
+    assert rt["status"] == 0 and rs["status"] == 0
+    nm = rt["phi"].shape[1]
+    for k in range(nm):
+        a, b = rt["phi"][:, k], rs["phi"][:, k]
+        assert np.linalg.norm(a - b) <= 1e-5 * max(np.linalg.norm(b), 1e-30), k
+    # exact definition Phi_i = V (U_r z_i) evaluated in FP64 from the device basis and vectors
+    m = rt["m"]
+    V = g.basis(0, m).double().cpu().numpy().T
+    ref = V @ rt["vec"][:, :nm]
+    for k in range(nm):
+        assert np.linalg.norm(rt["phi"][:, k] - ref[:, k]) <= 1e-5 * np.linalg.norm(ref[:, k])
+
+
+def test_async_indicator_records():
+    """Asynchronous pushes with indicator_every = 4: the side-stream eigensolves leave one record
+    per scheduled push, equal to the oracle's indicator at that point (Sec. 3.2.3)."""
+    import oracle as orc
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    spec = synth.config2(6, G=48, N=17)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f64")
+    g = FoaDMD(spec.n, 17, "f64", indicator_every=4, n_lead=3)
+    oo = orc.FoaOracle(spec.n, 17)
+    want = {}
+    for t in range(17):
+        assert g.push(Xd[t], info=(t == 0))[0] == 0
+        oo.push(Xr[:, t])
+        if (t + 1) % 4 == 0:
+            want[t + 1] = oo.eig(0.0)["indicator"][:3].max()
+    recs = g.indicators()
+    assert [r[0] for r in recs] == [4, 8, 12, 16]
+    for p, m, v in recs:
+        assert m == p - 1
+        assert abs(v - want[p]) <= 1e-7 * want[p] + 1e-14
+    assert g.indicators() == []
