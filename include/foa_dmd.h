@@ -203,6 +203,32 @@ int foa_dmd_reset(foa_dmd_t *h);
 int foa_dmd_save(foa_dmd_t *h, const char *path);
 int foa_dmd_load(const char *path, const foa_dmd_opts *opts, foa_dmd_t **out);
 
+/*
+ * One push that allocates no device memory, for callers that cannot call cudaMalloc at that
+ * point (an arena or pool owns all device memory, a host application forbids allocation on its
+ * hot path, or the work is issued into a region captured for replay).  The paper has no
+ * counterpart: it is the arithmetic of foa_dmd_push (Alg. 4 with p = 1) on buffers the caller
+ * owns, with the library's per-push scratch in a fixed file-scope device array instead of
+ * allocated memory.
+ *   V:        device, row-tiled basis as described at foa_dmd_get_basis (n rounded up to a
+ *             multiple of 32 rows, k_max columns per tile, storage dtype, zero-initialised);
+ *   Hbar, beta: device, k_max x k_max FP64 column-major (zero-initialised before the first push);
+ *   q:        current number of basis vectors (0 for the first snapshot);
+ *   x_dev:    device, the snapshot (n elements, storage dtype, 16-byte aligned);
+ *   w_dev:    device, working vector of ceil(n/32)*32 elements (FP32, or FP64 for FP64 storage),
+ *             zero-initialised once; on return it holds the unnormalised new direction;
+ *   info:     host, result of the push (q after the push, h_last, status).
+ * Limits: k_max <= 512 (384 for FP64); the scratch array holds the partial sums of at most 1024
+ * CTAs (about 4.8 MB, kept by every GPU that loads the library until the process exits).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * should therefore come before any stream capture.  Every call shares the array and clears
+ * what must start at zero; calls that overlap on the GPU (different streams or threads) race
+ * on it.  The call synchronises cuda_stream before returning.  Errors as for foa_dmd_push.
+ */
+int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, void *V, double *Hbar, double *beta,
+                         int32_t q, const void *x_dev, void *w_dev, double breakdown_tol, void *cuda_stream,
+                         foa_dmd_push_info *info);
+
 /* Free all resources of the handle (synchronises its stream). NULL is ignored. */
 void foa_dmd_destroy(foa_dmd_t *h);
 

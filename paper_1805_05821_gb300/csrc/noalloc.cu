@@ -1,0 +1,115 @@
+// One push without any device allocation: foa_dmd_push_noalloc.
+//
+// Some callers cannot allocate device memory at the point where they need the update: code
+// running under a memory pool or arena that owns all device memory, plug-ins whose host
+// application forbids cudaMalloc/cudaFree on its hot path (they may synchronise the device or
+// fragment a carefully sized heap), or code replayed inside a captured CUDA graph region that was
+// set up before.  For them this entry point performs the same push as foa_dmd_push on buffers the
+// caller already owns; the library's own per-push scratch (device state, beta_pre/h/s vectors,
+// the per-CTA partial sums of the cross-CTA reduction and their counters) lives in one
+// file-scope __device__ array of fixed size instead of memory obtained with cudaMalloc.
+#include <cstring>
+
+#include "api_internal.cuh"
+#include "push_kernels.cuh"
+
+namespace foa {
+namespace na {
+
+constexpr int kMaxGrid = 1024;                 // CTAs of one streaming pass
+constexpr int kGroups = kMaxGrid / kGroup + 1;
+constexpr size_t kStateBytes = 1024;           // DevState, rounded up
+constexpr size_t kVecBytes = 3 * size_t(kMaxK) * 8;
+constexpr size_t kPartBytes = size_t(kMaxGrid) * (kMaxK + 1) * 8;
+constexpr size_t kGpartBytes = size_t(kGroups) * (kMaxK + 1) * 8;
+constexpr size_t kCountBytes = 1024;
+constexpr size_t kScratchBytes = kStateBytes + kVecBytes + kPartBytes + kGpartBytes + kCountBytes;  // ~4.8 MB
+
+// The scratch shared by every call on a device (held until the process exits).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Device address of g_scratch per device, looked up once per device.
+static void *g_addr[64];
+
+__global__ void init_state_kernel(DevState *st, int q, int stopped) {
+  if (threadIdx.x == 0) {
+    st->q = q;
+    st->stopped = stopped;
+  }
+}
+
+}  // namespace na
+}  // namespace foa
+
+using namespace foa;
+using namespace foa::na;
+
+extern "C" int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, void *V, double *Hbar, double *beta,
+                                    int32_t q, const void *x_dev, void *w_dev, double breakdown_tol,
+                                    void *cuda_stream, foa_dmd_push_info *info) {
+  if (n < 1 || k_max < 2 || k_max > max_kmax_for(dtype) || dtype < 0 || dtype > 2 || !V || !Hbar || !beta || !x_dev ||
+      !w_dev || !info || q < 0)
+    return FOA_DMD_EINVAL;
+  if (q >= k_max) return FOA_DMD_EFULL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FOA_DMD_ECUDA;
+  int sms = 0;
+  int rc = check_device(&sms);
+  if (rc) return rc;
+  if (!g_addr[dev]) {
+    // first call on this device: resolve the array's device address (must precede any capture)
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return FOA_DMD_ECUDA;
+    g_addr[dev] = p;
+  }
+  unsigned char *base = static_cast<unsigned char *>(g_addr[dev]);
+  DevState *st = reinterpret_cast<DevState *>(base);
+  double *vec = reinterpret_cast<double *>(base + kStateBytes);
+  double *partials = reinterpret_cast<double *>(base + kStateBytes + kVecBytes);
+  double *gpart = reinterpret_cast<double *>(base + kStateBytes + kVecBytes + kPartBytes);
+  uint32_t *gcount = reinterpret_cast<uint32_t *>(base + kStateBytes + kVecBytes + kPartBytes + kGpartBytes);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+  // A stand-in handle that points at the caller's buffers and the static scratch.
+  foa_dmd h;
+  foa_dmd_opts_default(&h.opts);
+  h.n = n;
+  h.kmax = k_max;
+  h.dtype = dtype;
+  h.ntiles = int((n + kTile - 1) / kTile);
+  h.nrows = int64_t(h.ntiles) * kTile;
+  h.sms = sms;
+  h.stream = s;
+  h.tol = breakdown_tol > 0.0 ? breakdown_tol : default_tol(dtype);
+  h.V = V;
+  h.w = w_dev;
+  h.H = Hbar;
+  h.B = beta;
+  h.pre = vec;
+  h.hvec = vec + kMaxK;
+  h.svec = vec + 2 * kMaxK;
+  h.partials = partials;
+  h.gpart = gpart;
+  h.gcount = gcount;
+  h.st = st;
+  h.q_host = q;
+  if (sms * h.geom.max_ctas_per_sm > kMaxGrid) return FOA_DMD_EINVAL;
+  // everything the kernels expect to start at zero
+  cudaError_t e = cudaMemsetAsync(st, 0, kStateBytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(gcount, 0, kCountBytes, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  foa::na::init_state_kernel<<<1, 32, 0, s>>>(st, q, 0);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_status(e);
+  rc = enqueue_push(&h, x_dev, false, nullptr);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(info, &st->info, sizeof(*info), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  int32_t err = 0;
+  e = cudaMemcpy(&err, &st->err, sizeof(err), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (err) return err;
+  h.V = h.w = nullptr;  // the stand-in owns nothing
+  return info->status < 0 ? FOA_DMD_ECUDA : info->status;
+}

@@ -80,6 +80,8 @@ def lib():
             "foa_dmd_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
             "foa_dmd_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(foa_dmd_opts), ctypes.POINTER(vp)]),
             "foa_dmd_destroy": (None, [vp]),
+            "foa_dmd_push_noalloc": (ctypes.c_int, [i64, i32, i32, vp, _DP, _DP, i32, vp, vp, d, vp,
+                                                    ctypes.POINTER(foa_dmd_push_info)]),
             "foa_dmd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "foa_dmd_profile": (ctypes.c_int, [vp, ctypes.c_int]),
             "foa_dmd_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(foa_dmd_kernel_stats)]),
@@ -221,6 +223,16 @@ def foa_dmd_eig(h, rank_tol, cap, n_modes=0, phi=None, ld_phi=0, vec_cols=0, wan
             m = res.m
             out["vec"] = (vr[:m * vc].reshape(vc, m).T + 1j * vi[:m * vc].reshape(vc, m).T)
     return out
+
+
+def foa_dmd_push_noalloc(n, k_max, dtype, V, Hbar, beta, q, x, w, breakdown_tol=0.0, stream=None):
+    """V, Hbar, beta, x, w: device tensors owned by the caller (see include/foa_dmd.h)."""
+    info = foa_dmd_push_info()
+    st = lib().foa_dmd_push_noalloc(int(n), int(k_max), DTYPES.get(dtype, dtype), _ptr(V),
+                                    ctypes.cast(ctypes.c_void_p(int(Hbar.data_ptr())), _DP),
+                                    ctypes.cast(ctypes.c_void_p(int(beta.data_ptr())), _DP), int(q), _ptr(x), _ptr(w),
+                                    float(breakdown_tol), _stream_ptr(stream), ctypes.byref(info))
+    return st, info
 
 
 def foa_dmd_reset(h):
