@@ -39,7 +39,7 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   const int64_t bpart = align_up(int64_t(R) * kTile * base_size, 128);
   const int64_t slot_bytes = vpart + bpart;
   int64_t off = 0;
-  const int64_t other = align_up(int64_t(R) * kTile * cs, 128) + align_up(int64_t(jcap + 1) * cs, 16) +
+  const int64_t other = align_up(2 * int64_t(R) * kTile * cs, 128) + align_up(int64_t(jcap + 1) * cs, 16) +
                         align_up(int64_t(jcap + 2) * 8, 16) + kConsumers * 8 + kConsumers * 8 + 2 * kMaxSlots * 8 +
                         64;
   // two CTAs per SM for FP32/BF16 while the column accumulators fit in registers (j <= 384) and
@@ -60,7 +60,7 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   a.base_off = int(vpart);
   off = slot_bytes * slots;
   a.off_ws = int(off);
-  off += align_up(int64_t(R) * kTile * cs, 128);
+  off += align_up(2 * int64_t(R) * kTile * cs, 128);
   a.off_coef = int(off);
   off += align_up(int64_t(jcap + 1) * cs, 16);
   a.off_dot = int(off);

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   unsigned char *slots = smem;
-  C *ws = reinterpret_cast<C *>(smem + a.off_ws);
+  C *wsb = reinterpret_cast<C *>(smem + a.off_ws);  // 2 x R*32 entries
   C *cf = reinterpret_cast<C *>(smem + a.off_coef);
   double *dot = reinterpret_cast<double *>(smem + a.off_dot);
   double *comb = reinterpret_cast<double *>(smem + a.off_comb);
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
   if (tid == 0) {
     for (int i = 0; i < a.slots; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
+      mbar_init(&empty[i], kWarps);  // every consumer warp releases the slot after its column sweep
     }
     sflag[0] = 0;
     sflag[1] = 0;
@@ -131,8 +131,6 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
   };
   int since_flush = 0;
   int it = 0;
-  int prev_slot = -1;
-  bool aborted = false;
 
   auto flush = [&]() {
     if constexpr (kDots) {
@@ -150,14 +148,14 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
 
   for (int s = blockIdx.x; s < a.nstages; s += gridDim.x, ++it) {
     const int slot = it % a.slots;
-    const int failed = mbar_wait(&full[slot], (it / a.slots) & 1) ? 0 : 1;
-    if (named_bar_or(2, kConsumers, failed)) {  // every consumer takes the same decision
-      aborted = true;
+    // Every thread waits for the stage itself.  A wait that runs out records the error and the
+    // CTA carries on (its results are discarded by the host); the barrier sequence stays the same
+    // for all threads, and after the first timeout no thread waits again, so nothing can hang.
+    if (!sflag[0] && !mbar_wait(&full[slot], (it / a.slots) & 1)) {
       sflag[0] = 1;
-      if (tid == 0) atomicExch(&st->err, FOA_DMD_ETIMEOUT);
-      break;
+      atomicExch(&st->err, FOA_DMD_ETIMEOUT);
     }
-    if (prev_slot >= 0 && tid == 0) mbar_arrive(&empty[prev_slot]);
+    C *ws = wsb + (it & 1) * (a.R * kTile);  // double buffer: the next row sweep may start early
     const int t0 = s * a.R;
     const int nt = min(a.R, a.ntiles - t0);
     const int RS = nt * kTile;
@@ -278,21 +276,9 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
         }
       }
     }
-    // the slot is released after the next stage's vote barrier (all consumers are past sweep 2)
-    prev_slot = slot;
-  }
-  if (prev_slot >= 0 && !aborted) {
-    named_bar_sync(1, kConsumers);
-    if (tid == 0) mbar_arrive(&empty[prev_slot]);
-  }
-
-  if (aborted) {
-    // wait for the copies already issued into slots this CTA will not consume
-    if (tid == 0) {
-      const int issued = sflag[1];
-      for (int k = it; k < issued; ++k) mbar_wait(&full[k % a.slots], (k / a.slots) & 1);
-    }
-    return;
+    // this warp is done with the slot
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);
   }
   flush();
   if constexpr (kNorm) nrm[tid] = double(nsum) - double(ncomp);

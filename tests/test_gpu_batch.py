@@ -125,4 +125,6 @@ def test_batched_equals_single_stream_structure():
     q2, st, H2, B2 = F.foa_dmd_batch_get_state(b, 0, 30)
     F.foa_dmd_batch_destroy(b)
     assert q1 == q2 == 30
-    assert rel(B2, B1) <= 1e-5 and rel(H2[:30, :29], H1[:30, :29]) <= 1e-4
+    # two FP32 summation orders: agreement to k_max u_fp32 kappa_2(X), like the oracle comparisons
+    tol = 30 * U["f32"] * kappa_of(B1, 30)
+    assert rel(B2, B1) <= tol and rel(H2[:30, :29], H1[:30, :29]) <= tol
