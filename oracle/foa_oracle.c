@@ -108,6 +108,9 @@ int foa_oracle_first(int64_t n, double *V, double *B, const double *x, double *o
  *   beta_{i,j+1}   = beta_pre_i + h_{i,j} beta_{j,j},  i = 1..j;
  *   beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}                                       (steps 16-18)
  * reorth = 0 drops the second Gram-Schmidt pass (s = 0, classical Gram-Schmidt once).
+ * reorth = 2 is the two-pass reading of the same step: h_{j+1,j} is taken from the Pythagorean
+ * identity ||w - V s||^2 = ||w||^2 - ||s||^2 (w after the first projection, s = V^T w), the form
+ * that lets a streaming implementation append v_{j+1} during the next snapshot's first pass.
  * A new direction is declared dependent (Sec. 3.2.4: h_{j+1,j} = 0 means psi_{j+1} lies in
  * span{psi_1..psi_j}) when h_{j+1,j} beta_{j,j} <= tol * ||psi_{j+1}||_2; then column j of
  * Hbar gets h with h_{j+1,j} = 0, V and beta are left alone, and ORACLE_BREAKDOWN returns.
@@ -146,6 +149,8 @@ int foa_oracle_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, int
   /* step 11 */
   gemv_n(n, j, V, ldv, h, y);
   for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];
+  double w1norm2 = 0.0;
+  if (reorth == 2) w1norm2 = dot_blocked(n, w, w, part);
   if (reorth) {
     /* step 12 */
     gemv_t(n, j, V, ldv, w, s, part);
@@ -156,7 +161,15 @@ int foa_oracle_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, int
     for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];
   }
   /* step 15 */
-  double nu = sqrt(dot_blocked(n, w, w, part));
+  double nu;
+  if (reorth == 2) {
+    double ss = 0.0;
+    for (int32_t i = 0; i < j; ++i) ss += s[i] * s[i];
+    double d = w1norm2 - ss;
+    nu = sqrt(d > 0.0 ? d : 0.0);
+  } else {
+    nu = sqrt(dot_blocked(n, w, w, part));
+  }
   double xn = sqrt(dot_blocked(n, x, x, part));
   out[0] = nu;
   out[1] = xn;
