@@ -62,6 +62,8 @@ def load(path):
     L.foa_oracle_first.restype = ctypes.c_int
     L.foa_oracle_step.argtypes = [i64, i32, P, i64, P, i32, P, i32, P, d, ctypes.c_int, P]
     L.foa_oracle_step.restype = ctypes.c_int
+    L.foa_oracle_qr_step.argtypes = [i64, i32, P, i64, P, i32, P, i32, P, d, ctypes.c_int, P]
+    L.foa_oracle_qr_step.restype = ctypes.c_int
     return L
 
 
@@ -89,7 +91,11 @@ def auto_rank_tol(storage, n_snapshots):
 class FoaOracle:
     """Streaming FOA-based DMD state (H, V, beta, q) of Algorithm 3 in FP64 on the host."""
 
-    def __init__(self, n, k_max, breakdown_tol=None, storage="f64", reorth=1, library=None):
+    def __init__(self, n, k_max, breakdown_tol=None, storage="f64", reorth=1, library=None, form="foa"):
+        """form: "foa" = Alg. 1 steps 5-18 as printed; "qr" = the QR view of the same push
+        (psi orthogonalised directly, beta column = [h; nu], Hbar column from Eq. matmulhbeta)."""
+        assert form in ("foa", "qr")
+        self.form = form
         self._L = library
         self.n, self.k_max = int(n), int(k_max)
         self.storage = storage
@@ -127,8 +133,9 @@ class FoaOracle:
             self.h_last.append(nrm.value)
             return "ok", nrm.value, nrm.value
         out = np.zeros(2)
-        st = L.foa_oracle_step(self.n, self.q, _ptr(self.V), self.n, _ptr(self.H), self.k_max,
-                               _ptr(self.B), self.k_max, _ptr(x), self.tol, self.reorth, _ptr(out))
+        step = L.foa_oracle_qr_step if self.form == "qr" else L.foa_oracle_step
+        st = step(self.n, self.q, _ptr(self.V), self.n, _ptr(self.H), self.k_max,
+                  _ptr(self.B), self.k_max, _ptr(x), self.tol, self.reorth, _ptr(out))
         if st == NOMEM:
             raise MemoryError
         if st == BREAKDOWN:
@@ -238,10 +245,10 @@ def mode_order(lam, c):
     return np.lexsort((-lam.imag, -np.abs(lam), -key))
 
 
-def run(X, k_max=None, breakdown_tol=None, storage="f64", reorth=1, library=None):
+def run(X, k_max=None, breakdown_tol=None, storage="f64", reorth=1, library=None, form="foa"):
     """Algorithm 1 (batch form) as a loop of streaming updates; returns the oracle state."""
     n, N = X.shape
-    o = FoaOracle(n, k_max or N, breakdown_tol, storage, reorth, library)
+    o = FoaOracle(n, k_max or N, breakdown_tol, storage, reorth, library, form)
     for t in range(N):
         st, _, _ = o.push(X[:, t])
         if st != "ok":

@@ -192,4 +192,73 @@ int foa_oracle_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, int
   return status;
 }
 
+/*
+ * The QR view of the same push (Sec. 3.1: FOA-based DMD computes a QR factorisation X = V beta
+ * of the snapshot matrix; App. B, Eq. matmulhbeta: beta_{:,2:j+1} = Hbar_j beta_j).  The new
+ * snapshot is orthogonalised directly (CGS2 on psi_{j+1}, no pre-vector):
+ *   h = V^T psi;  w = psi - V h;  s = V^T w;  h = h + s;  w = w - V s;  nu = ||w||_2
+ *   beta_{1:j,j+1} = h,  beta_{j+1,j+1} = nu,  v_{j+1} = w / nu
+ * and column j of Hbar follows from column j+1 of beta by forward substitution in
+ * beta_{:,j+1} = sum_{l<=j} Hbar_{:,l} beta_{l,j}:
+ *   Hbar_{i,j} = (beta_{i,j+1} - sum_{l=max(1,i-1)}^{j-1} Hbar_{i,l} beta_{l,j}) / beta_{j,j},  i <= j
+ *   Hbar_{j+1,j} = beta_{j+1,j+1} / beta_{j,j}
+ * In exact arithmetic this is the same Hbar as foa_oracle_step.  Breakdown reading as there:
+ * nu <= tol * ||psi||_2 (nu is the distance of psi from span V), then column j of Hbar gets its
+ * first j entries with Hbar_{j+1,j} = 0 and V, beta are left alone.
+ * reorth = 0 drops s.  out[0] = Hbar_{j+1,j}, out[1] = ||psi||_2.
+ */
+int foa_oracle_qr_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, int32_t ldh, double *B,
+                       int32_t ldb, const double *x, double tol, int reorth, double *out) {
+  int64_t nb = nblocks_of(n);
+  double *w = (double *)malloc(sizeof(double) * (size_t)n);
+  double *y = (double *)malloc(sizeof(double) * (size_t)n);
+  double *part = (double *)malloc(sizeof(double) * (size_t)(nb * (j > 1 ? j : 1)));
+  double *h = (double *)calloc((size_t)j, sizeof(double));
+  double *s = (double *)calloc((size_t)j, sizeof(double));
+  if (!w || !y || !part || !h || !s) {
+    free(w); free(y); free(part); free(h); free(s);
+    return ORACLE_NOMEM;
+  }
+#define HB(i, l) H[(int64_t)(l) * ldh + (i)]
+#define BT(i, l) B[(int64_t)(l) * ldb + (i)]
+  const int32_t jc = j - 1;
+  gemv_t(n, j, V, ldv, x, h, part);
+  gemv_n(n, j, V, ldv, h, y);
+  for (int64_t r = 0; r < n; ++r) w[r] = x[r] - y[r];
+  if (reorth) {
+    gemv_t(n, j, V, ldv, w, s, part);
+    for (int32_t i = 0; i < j; ++i) h[i] = h[i] + s[i];
+    gemv_n(n, j, V, ldv, s, y);
+    for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];
+  }
+  double nu = sqrt(dot_blocked(n, w, w, part));
+  double xn = sqrt(dot_blocked(n, x, x, part));
+  double bjj = BT(jc, jc);
+  /* column j of Hbar from beta_{1:j,j+1} = h by forward substitution */
+  for (int32_t i = 0; i < j; ++i) {
+    int32_t l0 = i == 0 ? 0 : i - 1;
+    double acc = 0.0;
+    for (int32_t l = l0; l <= j - 2; ++l) acc += HB(i, l) * BT(l, jc);
+    HB(i, jc) = (h[i] - acc) / bjj;
+  }
+  int status = ORACLE_OK;
+  if (!(nu > tol * xn)) {
+    HB(j, jc) = 0.0;
+    out[0] = 0.0;
+    status = ORACLE_BREAKDOWN;
+  } else {
+    HB(j, jc) = nu / bjj;
+    out[0] = nu / bjj;
+    double *vn = V + (int64_t)j * ldv;
+    for (int64_t r = 0; r < n; ++r) vn[r] = w[r] / nu;
+    for (int32_t i = 0; i < j; ++i) BT(i, j) = h[i];
+    BT(j, j) = nu;
+  }
+  out[1] = xn;
+#undef HB
+#undef BT
+  free(w); free(y); free(part); free(h); free(s);
+  return status;
+}
+
 int foa_oracle_block_rows(void) { return ORACLE_BLOCK; }

@@ -28,8 +28,8 @@ def match_eigs(a, b):
     return D[ri, ci], ci
 
 
-def run_oracle(X, k_max=None, tol=None, library=None, reorth=1):
-    return oracle.run(X, k_max, tol, "f64", reorth, library)
+def run_oracle(X, k_max=None, tol=None, library=None, reorth=1, form="foa"):
+    return oracle.run(X, k_max, tol, "f64", reorth, library, form)
 
 
 # ------------------------------------------------------------------ closed forms
@@ -339,6 +339,45 @@ def test_two_pass_reading_agrees():
         assert np.linalg.norm(np.eye(q) - b.V[:, :q].T @ b.V[:, :q], 2) <= 10 * X.shape[1] * U64 * 10
 
 
+def test_qr_view_is_the_householder_qr():
+    """The QR view (Sec. 3.1: X = V beta with V orthonormal and beta upper triangular): beta equals
+    LAPACK's R of X and V its Q, once the signs are fixed so that diag(R) > 0."""
+    X = np.random.default_rng(5).standard_normal((500, 24))
+    o = run_oracle(X, form="qr")
+    assert o.q == 24
+    Q, R = np.linalg.qr(X)
+    sg = np.sign(np.diag(R))
+    Q, R = Q * sg[None, :], R * sg[:, None]
+    assert np.linalg.norm(o.B[:24, :24] - R) <= 50 * U64 * np.linalg.norm(R)
+    assert np.linalg.norm(o.V[:, :24] - Q) <= 50 * U64 * 24
+    assert np.all(np.tril(o.B[:24, :24], -1) == 0.0)
+
+
+def test_qr_view_equals_foa_form():
+    """Eq. matmulhbeta: the Hbar the QR view forms from beta is the Hbar of Alg. 1 (equal in exact
+    arithmetic); beta of the QR view is beta of Alg. 1 (both are R of X).  Checked to rounding on a
+    well-conditioned and an ill-conditioned (Vandermonde) sequence, with the O(eps kappa) law."""
+    for X in (np.random.default_rng(6).standard_normal((300, 16)), synth.vandermonde_sequence(10, seed=4)[1]):
+        a = run_oracle(X, tol=1e-300)
+        b = run_oracle(X, tol=1e-300, form="qr")
+        assert a.q == b.q
+        q, m = a.q, a.m
+        s = np.linalg.svd(X[:, :q], compute_uv=False)
+        kap = s[0] / s[-1]
+        assert np.linalg.norm(a.B[:q, :q] - b.B[:q, :q]) <= 1e3 * U64 * kap * np.linalg.norm(a.B[:q, :q])
+        assert np.linalg.norm(a.H[:m + 1, :m] - b.H[:m + 1, :m]) <= 1e3 * U64 * kap * np.linalg.norm(a.H[:m + 1, :m])
+
+
+def test_qr_view_planted_breakdown():
+    """Planted rank-10 map: the QR view also stops at push 11 and gives the planted eigenvalues."""
+    spec = synth.config1(0)
+    X = synth.snapshots(spec)
+    o = run_oracle(X, k_max=32, form="qr")
+    assert o.stopped and o.q == 10 and o.m == 10
+    d, _ = match_eigs(o.eig(0.0)["lam"], spec.lam)
+    assert d.max() <= 1e-9
+
+
 # ------------------------------------------------------------------ planted mistakes
 MUTANTS = {
     "drop_second_projection": ("gemv_n(n, j, V, ldv, s, y);\n    for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];",
@@ -350,11 +389,21 @@ MUTANTS = {
     "beta_pre_index": ("int32_t l0 = i == 0 ? 0 : i - 1;", "int32_t l0 = i;"),
     "no_divide_by_bjj": ("w[r] = (x[r] - y[r]) / bjj;", "w[r] = (x[r] - y[r]);"),
     "diag_missing_bjj": ("BT(j, j) = nu * bjj;", "BT(j, j) = nu;"),
+    "qr_hbar_sign": ("HB(i, jc) = (h[i] - acc) / bjj;", "HB(i, jc) = (h[i] + acc) / bjj;"),
+    "qr_subdiag_missing_bjj": ("HB(j, jc) = nu / bjj;", "HB(j, jc) = nu;"),
+    "qr_beta_diag": ("    BT(j, j) = nu;\n", "    BT(j, j) = nu * bjj;\n"),
+    "qr_hbar_index": ("acc += HB(i, l) * BT(l, jc);\n    HB(i, jc) = (h[i] - acc) / bjj;",
+                      "acc += HB(i, l) * BT(jc, l);\n    HB(i, jc) = (h[i] - acc) / bjj;"),
 }
 
 
 def _pins_pass(library):
-    """Run a compact set of pins against an oracle library; True when all of them hold."""
+    """Run a compact set of pins against an oracle library, for both forms of the push; True when
+    all of them hold."""
+    return _form_pins_pass(library, "foa") and _form_pins_pass(library, "qr")
+
+
+def _form_pins_pass(library, form):
     try:
         rng = np.random.default_rng(3)
         n, N = 60, 12
@@ -363,7 +412,7 @@ def _pins_pass(library):
         X[:, 0] = rng.standard_normal(n)
         for t in range(1, N):
             X[:, t] = A @ X[:, t - 1]
-        o = run_oracle(X, library=library)
+        o = run_oracle(X, library=library, form=form)
         if o.q != N:
             return False
         q = o.q
@@ -378,7 +427,7 @@ def _pins_pass(library):
             return False
         # ill-conditioned sequence (Vandermonde map): the second Gram-Schmidt pass matters here
         A2, X2 = synth.vandermonde_sequence(10, seed=1)
-        o2 = oracle.FoaOracle(50, 10, breakdown_tol=1e-300, library=library)
+        o2 = oracle.FoaOracle(50, 10, breakdown_tol=1e-300, library=library, form=form)
         for t in range(10):
             o2.push(X2[:, t])
         q2 = o2.q
