@@ -36,6 +36,10 @@ METRIC = "snapshots/s ingested at n=67M,k≤384; HBM GB/s vs peak; eig rel. err 
 UNIT = "snapshots/s"
 FALLBACK_HBM_GBS = 6800.0
 BREAKDOWN_TOL = 1e-12
+PASS_NAMES = {1: ("A", "B", "C", "other"), 2: ("A2 (lagged append + first projection)", "B2 (second projection + commit)",
+                                            "unused", "other")}
+PUSH_FORM = {1: "CGS2, three passes over V per push (Alg. 1 steps 9-15)",
+             2: "CGS2 read as two passes over V per push (h_{j+1,j} by Pythagoras, lagged append)"}
 
 
 def parse():
@@ -48,6 +52,9 @@ def parse():
     p.add_argument("--snapshots", type=int, default=384)
     p.add_argument("--indicator-every", type=int, default=16)
     p.add_argument("--modes", type=int, default=32)
+    p.add_argument("--reorth", type=int, default=1, choices=[1, 2],
+                   help="1: CGS2 in three passes over V per push; 2: the two-pass reading (Pythagorean "
+                        "h_{j+1,j}, new column appended during the next push's first pass)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--sample-grid", type=int, default=32, help="grid of the CPU-oracle sample")
@@ -170,7 +177,7 @@ def traffic_ratio():
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(G, N, every, n_modes, full_n):
+def oracle_sample(G, N, every, n_modes, full_n, reorth=1):
     """The FP64 oracle (C push, OpenMP over fixed row blocks; LAPACK eig) on the same generator at
     a smaller grid: the same N pushes, indicator schedule, truncated eig and modes.  The push
     cost is linear in n, so snapshots/s at the full n is the measured rate times n_sample/n."""
@@ -179,7 +186,7 @@ def oracle_sample(G, N, every, n_modes, full_n):
     spec = synth.config5(0, G=G, N=N)
     X = synth.snapshots(spec, np.float32).astype(np.float64)
     t0 = time.perf_counter()
-    o = oracle.FoaOracle(spec.n, N, breakdown_tol=BREAKDOWN_TOL, storage="f32")
+    o = oracle.FoaOracle(spec.n, N, breakdown_tol=BREAKDOWN_TOL, storage="f32", reorth=reorth)
     for t in range(N):
         st, _, _ = o.push(X[:, t])
         if st != "ok":
@@ -203,7 +210,7 @@ def run_reference(args):
     full_n = 4 * args.grid ** 3
     vals = []
     for i in range(args.warmup + args.steps):
-        s = oracle_sample(args.sample_grid, args.snapshots, args.indicator_every, args.modes, full_n)
+        s = oracle_sample(args.sample_grid, args.snapshots, args.indicator_every, args.modes, full_n, args.reorth)
         if i >= args.warmup:
             vals.append(s)
     v = statistics.median([s["value"] for s in vals])
@@ -256,6 +263,7 @@ def main():
     # 1/eps_fp32 on purpose, to exercise rank truncation); the default breakdown test (sqrt(u_fp32))
     # would stop the stream there, so the run keeps every snapshot.
     opts.breakdown_tol = BREAKDOWN_TOL
+    opts.reorth = args.reorth
     h = F.foa_dmd_create(n, N, "f32", opts)
     ld_phi = (n + 3) // 4 * 4
     nm = args.modes
@@ -311,11 +319,16 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None,
             "traffic": (ratio * pass_bytes / pass_launches) if (ratio and pass_launches) else None,
-            "kernel": "pass_kernel (streaming passes A/B/C over V)",
+            "kernel": ("pass_kernel (streaming passes A/B/C over V)" if args.reorth == 1 else
+                       "lag_kernel + pass_kernel (the two streaming passes over V)"),
             "algorithmic_bytes_per_launch": pass_bytes / pass_launches if pass_launches else None,
             "avg_launch_ms": pass_ms / pass_launches if pass_launches else None,
             "share_of_step": pass_ms / (secs * 1e3) if secs > 0 else None,
-            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback"}
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+            "per_pass": {name: {"launches": stats["launches"][k],
+                                "avg_ms": stats["ms"][k] / stats["launches"][k],
+                                "GBps": stats["bytes"][k] / (stats["ms"][k] / 1e3) / 1e9}
+                         for k, name in enumerate(PASS_NAMES[args.reorth]) if stats["launches"][k] and stats["ms"][k] > 0}}
     gpu_launches = stats["total_launches"]
     # planted-truth check of the leading eigenvalues (err against the generating map)
     lam = res["lam"]
@@ -331,7 +344,8 @@ def main():
            "warmup": args.warmup, "ms_per_step": secs_max * 1e3 / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": workload_name(G, N), "n": n, "N": N, "l2": "inputs (N x n FP32 snapshots, "
-                      f"{N * n * 4 / 1e9:.0f} GB) exceed L2; no flush needed", "parallelism": "independent stream per GPU"},
+                      f"{N * n * 4 / 1e9:.0f} GB) exceed L2; no flush needed", "parallelism": "independent stream per GPU",
+                      "push": PUSH_FORM[args.reorth]},
            "roofline": roof, "gpu_launches": gpu_launches, "clocks": clocks,
            "accuracy": {"rank": res["r"], "m": res["m"], "leading32_rel_err_vs_planted": rel_planted}}
     # ---- end to end through the public API with host buffers (pinned), copies in the timed region
@@ -342,12 +356,12 @@ def main():
     out["e2e"] = e2e
     # ---- CPU oracle baseline (rank 0) and the FP32-vs-FP64 eigenvalue error on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(args.sample_grid, N, args.indicator_every, nm, n)
+        s = oracle_sample(args.sample_grid, N, args.indicator_every, nm, n, args.reorth)
         out["cpu_baseline"] = {"value": s["value"], "unit": UNIT, "cores": s["cores"], "kind": "oracle",
                                "sample": f"FP64 C oracle (OpenMP, fixed row blocks) on fields4x{args.sample_grid}^3 "
                                          f"(n={s['n_sample']}), N={N}, same schedule/eig/modes; "
                                          f"{s['seconds']:.1f} s, rate scaled by n_sample/n"}
-        out["accuracy"].update(sample_eig_accuracy(s, F, torch, N, nm))
+        out["accuracy"].update(sample_eig_accuracy(s, F, torch, N, nm, args.reorth))
     F.foa_dmd_destroy(h)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -357,13 +371,13 @@ def main():
     return 0
 
 
-def sample_eig_accuracy(s, F, torch, N, nm):
+def sample_eig_accuracy(s, F, torch, N, nm, reorth=1):
     """Relative error of the leading eigenvalues of the FP32 GPU path against the FP64 oracle on the
     same (FP32-rounded) sample inputs."""
     X = s["X"]
     n = X.shape[0]
     Xd = torch.from_numpy(np.ascontiguousarray(X.T).astype(np.float32)).cuda()
-    g = F.FoaDMD(n, N, "f32", breakdown_tol=BREAKDOWN_TOL)
+    g = F.FoaDMD(n, N, "f32", breakdown_tol=BREAKDOWN_TOL, reorth=reorth)
     for t in range(N):
         st, _ = g.push(Xd[t], info=False)
     res = g.eig(-1.0)
@@ -449,12 +463,14 @@ def _match_rel(a, b):
 
 
 def run_forms(args):
-    """Secondary measurement: the FP64, FP32 and BF16 storage forms on the 1024^2 waves workload
+    """Secondary measurement: the FP64, FP32 and BF16 storage forms (and the two-pass push in FP64
+    and FP32) on the 1024^2 waves workload
     (n = 2^20, N = 200, 20 damped waves, noise 1e-6) -- snapshots/s (pushes + eig, CUDA events)
     and the relative error of the 20 leading eigenvalues against the FP64 oracle on the same
     storage-rounded inputs and against the planted eigenvalues; then a kappa sweep of the
     precision forms (waves3d, 64^3 grid, N = 200, 100 undamped waves with amplitudes
-    kappa_t^{-(m-1)/99}): normwise H-bar and beta errors against the oracle in units of u*kappa_2."""
+    kappa_t^{-(m-1)/99}): normwise H-bar and beta errors against the oracle (the paper's three-pass
+    step) in units of u*kappa_2, for the three-pass push, the two-pass push and the QR view."""
     import torch
     import oracle
     from paper_1805_05821_gb300 import build, synth
@@ -473,8 +489,8 @@ def run_forms(args):
         torch.cuda.synchronize()
         return X
 
-    def run_gpu(Xd, n, N, dt, tol):
-        g = F.FoaDMD(n, N, dt, breakdown_tol=tol)
+    def run_gpu(Xd, n, N, dt, tol, reorth=1, form=0):
+        g = F.FoaDMD(n, N, dt, breakdown_tol=tol, reorth=reorth, form=form)
         Xc = Xd.to(tdt[dt]).contiguous()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -493,8 +509,9 @@ def run_forms(args):
            "data": "synthetic", "forms": {}, "kappa_sweep": []}
     spec = synth.config2(0)
     Xd = device_snapshots(spec)
-    for dt in ("f64", "f32", "bf16"):
-        res, q, H, B, secs, Xr = run_gpu(Xd, spec.n, spec.N, dt, 1e-12)
+    for dt, ro_ in (("f64", 1), ("f32", 1), ("bf16", 1), ("f64", 2), ("f32", 2)):
+        res, q, H, B, secs, Xr = run_gpu(Xd, spec.n, spec.N, dt, 1e-12, ro_)
+        # the oracle runs the paper's three-pass CGS2 step in both cases
         o = oracle.FoaOracle(spec.n, spec.N, breakdown_tol=1e-12, storage=dt)
         for t in range(spec.N):
             if o.push(Xr[:, t])[0] != "ok":
@@ -510,14 +527,15 @@ def run_forms(args):
                  "beta_rel_err_vs_oracle": float(np.linalg.norm(B[:q, :q] - o.B[:q, :q]) / np.linalg.norm(o.B[:q, :q]))}
         sv = np.linalg.svd(o.B[:q, :q], compute_uv=False)
         entry["kappa2"] = float(sv[0] / sv[-1])
-        out["forms"][dt] = entry
+        out["forms"][dt if ro_ == 1 else dt + "_two_pass"] = entry
     del Xd
     for kap in (1e2, 1e4, 1e6, 1e8):
         sp = synth.waves(64, 3, 1, 200, 100, 1, sigma=None, omega=np.pi * (np.arange(1, 101) - 0.5) / 100,
                          amp=kap ** (-np.arange(100) / 99.0), kmax=31, name=f"waves3d 64^3 kappa_t={kap:g}")
         Xd = device_snapshots(sp)
-        for dt in ("f32", "bf16"):
-            res, q, H, B, secs, Xr = run_gpu(Xd, sp.n, sp.N, dt, 1e-12)
+        for dt, ro_, fm in (("f32", 1, 0), ("bf16", 1, 0), ("f32", 2, 0), ("bf16", 2, 0), ("f32", 1, 1),
+                            ("bf16", 1, 1)):
+            res, q, H, B, secs, Xr = run_gpu(Xd, sp.n, sp.N, dt, 1e-12, ro_, fm)
             o = oracle.FoaOracle(sp.n, sp.N, breakdown_tol=1e-12, storage=dt)
             for t in range(sp.N):
                 if o.push(Xr[:, t])[0] != "ok":
@@ -527,7 +545,9 @@ def run_forms(args):
             k2 = float(sv[0] / sv[-1])
             eh = float(np.linalg.norm(H[:m + 1, :m] - o.H[:m + 1, :m]) / np.linalg.norm(o.H[:m + 1, :m]))
             eb = float(np.linalg.norm(B[:o.q, :o.q] - o.B[:o.q, :o.q]) / np.linalg.norm(o.B[:o.q, :o.q]))
-            out["kappa_sweep"].append({"kappa_t": kap, "dtype": dt, "kappa2": k2, "q": q, "hbar_rel_err": eh,
+            out["kappa_sweep"].append({"kappa_t": kap, "dtype": dt,
+                                       "push": "qr_view" if fm else ("two_pass" if ro_ == 2 else "three_pass"),
+                                       "kappa2": k2, "q": q, "hbar_rel_err": eh,
                                        "beta_rel_err": eb, "hbar_err_over_u_kappa": eh / (u[dt] * k2),
                                        "snapshots_per_s": sp.N / secs})
         del Xd

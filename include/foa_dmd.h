@@ -56,7 +56,14 @@ typedef enum {
 
 typedef struct {
   int32_t reorth;          /* 1 (default): classical Gram-Schmidt with one reorthogonalization
-                              (CGS2, Alg. 1 steps 10-14); 0: one classical Gram-Schmidt pass */
+                              (CGS2, Alg. 1 steps 10-14); 0: one classical Gram-Schmidt pass;
+                              2: the same CGS2 step read as two passes over V per push:
+                              h_{j+1,j} from ||w||^2 - ||s||^2 (w after the first projection,
+                              s = V^T w, Pythagoras for orthonormal V), and v_{j+1} written
+                              while the next push streams V.  H-bar, beta and q are committed
+                              at the end of each push; the newest basis column is written by
+                              the next push or before V is read (foa_dmd_get_basis,
+                              foa_dmd_save, foa_dmd_eig modes).  Other values: EINVAL. */
   double breakdown_tol;    /* breakdown when h_{j+1,j} beta_{j,j} <= tol * ||x||_2; <= 0 selects
                               the default sqrt(u) of the storage dtype (2^-26.5, 2^-12, 2^-4) */
   int32_t indicator_every; /* 0 (default): push reports h_{j+1,j} only; m > 0: every m-th push
@@ -66,6 +73,14 @@ typedef struct {
   double indicator_rank_tol; /* rank_tol for the scheduled eigensolve (0: no truncation,
                                 < 0: automatic, as for foa_dmd_eig) */
   void *cuda_stream;       /* cudaStream_t for all work of the handle; NULL = default stream */
+  int32_t form;            /* 0 (default): the push as Alg. 1 steps 5-18 print it (pre-vector
+                              w = (psi - V beta_pre)/beta_jj, beta column from beta_pre + h beta_jj);
+                              1: the QR view of the same push (Sec. 3.1): psi is orthogonalised
+                              directly (h = V^T psi, CGS2 or CGS1 as reorth says), the beta column
+                              is [h; nu] and the Hbar column comes from beta_{:,2:} = Hbar beta
+                              (App. B, Eq. matmulhbeta) by forward substitution.  Equal in exact
+                              arithmetic; the rounding differs.  form = 1 takes reorth 0 or 1;
+                              other combinations: EINVAL.  The batched streams use form 0. */
 } foa_dmd_opts;
 
 /* Fill opts with the defaults listed above. */

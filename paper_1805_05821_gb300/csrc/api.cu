@@ -25,6 +25,7 @@ int max_kmax_for(int dtype) { return dtype == FOA_DMD_F64 ? 384 : kMaxK; }
 bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n, int ntiles, int sms, PassArgs &a,
                     int &grid) {
   const int s = dtype_size(dtype), cs = compute_size(dtype);
+  const bool lag = (mode == PASS_A2 || mode == PASS_FIN);
   const bool basex = (mode == PASS_A || mode == PASS_FIRST);
   const int base_size = basex ? s : cs;
   const int jj = (mode == PASS_FIRST) ? 0 : jcap;
@@ -36,16 +37,21 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
     while (R * 2 <= kMaxR && (R * 2) * tile_bytes <= g.stage_bytes) R *= 2;
   }
   const int64_t vpart = align_up(R * tile_bytes, 128);
-  const int64_t bpart = align_up(int64_t(R) * kTile * base_size, 128);
+  // the lagged first pass also stages the x slice (storage type) and the w' slice (compute type)
+  const int64_t bpart = lag ? align_up(int64_t(R) * kTile * s, 128) + align_up(int64_t(R) * kTile * cs, 128)
+                            : align_up(int64_t(R) * kTile * base_size, 128);
   const int64_t slot_bytes = vpart + bpart;
-  int64_t off = 0;
-  const int64_t other = align_up(2 * int64_t(R) * kTile * cs, 128) + align_up(int64_t(jcap + 1) * cs, 16) +
-                        align_up(int64_t(jcap + 2) * 8, 16) + kConsumers * 8 + kConsumers * 8 + 2 * kMaxSlots * 8 +
-                        64;
+  const int64_t ws_bytes = align_up(2 * int64_t(R) * kTile * cs, 128);
+  const int64_t vnew_bytes = lag ? align_up(int64_t(R) * kTile * cs, 128) : 0;
+  const int64_t cf_bytes = align_up(int64_t(jcap + 8) * cs, 16);
+  const int64_t cf2_bytes = lag ? cf_bytes : 0;
+  const int64_t comb_bytes = lag ? 2 * kConsumers * 8 : kConsumers * 8;
+  const int64_t other = ws_bytes + vnew_bytes + cf_bytes + cf2_bytes + align_up(int64_t(jcap + 2) * 8, 16) +
+                        comb_bytes + kConsumers * 8 + 2 * kMaxSlots * 8 + 64;
   // two CTAs per SM for FP32/BF16 while the column accumulators fit in registers (j <= 384) and
   // two slots fit in half the shared memory; otherwise one CTA per SM with a deeper ring
   const int nc = pass_nc_for(jcap);
-  const bool two = (cs == 4) && (mode == PASS_C || mode == PASS_FIRST || nc <= 48) &&
+  const bool two = (cs == 4) && (mode == PASS_C || mode == PASS_FIRST || mode == PASS_FIN || nc <= 48) &&
                    (2 * slot_bytes + other <= g.smem_budget2) && g.max_ctas_per_sm >= 2;
   const int64_t budget = two ? g.smem_budget2 : g.smem_budget;
   const int64_t inflight = two ? g.inflight_bytes / 2 : g.inflight_bytes;
@@ -58,15 +64,20 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   a.slots = slots;
   a.slot_bytes = int(slot_bytes);
   a.base_off = int(vpart);
-  off = slot_bytes * slots;
+  a.base2_off = lag ? int(vpart + align_up(int64_t(R) * kTile * s, 128)) : 0;
+  int64_t off = slot_bytes * slots;
   a.off_ws = int(off);
-  off += align_up(2 * int64_t(R) * kTile * cs, 128);
+  off += ws_bytes;
+  a.off_vnew = int(off);
+  off += vnew_bytes;
   a.off_coef = int(off);
-  off += align_up(int64_t(jcap + 1) * cs, 16);
+  off += cf_bytes;
+  a.off_coef2 = int(off);
+  off += cf2_bytes;
   a.off_dot = int(off);
   off += align_up(int64_t(jcap + 2) * 8, 16);
   a.off_comb = int(off);
-  off += kConsumers * 8;
+  off += comb_bytes;
   a.off_norm = int(off);
   off += kConsumers * 8;
   a.off_bar = int(off);
@@ -109,6 +120,7 @@ extern "C" void foa_dmd_opts_default(foa_dmd_opts *o) {
   o->n_lead = 32;
   o->indicator_rank_tol = 0.0;
   o->cuda_stream = nullptr;
+  o->form = 0;
 }
 
 namespace foa {
@@ -238,6 +250,7 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
   a.x = x;
   a.w = h->w;
   a.coef = coef;
+  a.coef2 = h->svec;
   a.partials = h->partials;
   a.gpart = h->gpart;
   a.gcount = h->gcount;
@@ -252,6 +265,7 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
   a.reorth = h->opts.reorth;
   a.x_aligned = x ? ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) : 0;
   a.batch = batch ? 1 : 0;
+  a.form = h->opts.form;
   a.tol = h->tol;
   const double s = dtype_size(h->dtype), cs = compute_size(h->dtype), n = double(h->n);
   double bytes = 0.0;
@@ -260,6 +274,10 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
     case PASS_A: bytes = n * jcap * s + n * s + n * cs; kind = 0; break;
     case PASS_B: bytes = n * jcap * s + 2 * n * cs; kind = 1; break;
     case PASS_C: bytes = n * jcap * s + 2 * n * cs; kind = 2; break;
+    // lagged first pass: V (jcap - 1 stored columns) + x + w' read, the new column and w written
+    case PASS_A2: bytes = n * (jcap - 1) * s + n * s + n * cs + n * s + n * cs; kind = 0; break;
+    case PASS_B2: bytes = n * jcap * s + 2 * n * cs; kind = 1; break;
+    case PASS_FIN: bytes = n * (jcap - 1) * s + n * cs + n * s; kind = 3; break;
     default: bytes = n * s; kind = 3; break;
   }
   ProfScope ps(h, kind, bytes);
@@ -283,6 +301,14 @@ int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_
       rc = cuda_status(launch_colwrite(h->dtype, h->V, x, true, h->st, h->n, h->nrows, h->kmax, h->sms, h->stream));
     }
     if (rc) return rc;
+  } else if (h->opts.reorth == 2) {
+    // two-pass push: the lagged first pass appends the column left pending by the previous push
+    // (if any) and projects x; the second pass commits h_{j+1,j} and leaves v_{j+1} pending
+    h->launches -= 1;  // no column write
+    rc = launch_pass_h(h, PASS_A2, jcap, x, h->pre, batch, info_out);
+    if (rc) return rc;
+    rc = launch_pass_h(h, PASS_B2, jcap, nullptr, h->hvec, batch, info_out);
+    if (rc) return rc;
   } else {
     rc = launch_pass_h(h, PASS_A, jcap, x, h->pre, batch, info_out);
     if (rc) return rc;
@@ -303,12 +329,20 @@ int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_
   return FOA_DMD_OK;
 }
 
+// Two-pass push: write the pending basis column (if any) before V is read outside a push.
+int flush_pending(foa_dmd *h) {
+  if (h->opts.reorth != 2 || h->q_host < 2) return FOA_DMD_OK;
+  return launch_pass_h(h, PASS_FIN, h->q_host, nullptr, nullptr, false, nullptr);
+}
+
 }  // namespace foa
 
 extern "C" int foa_dmd_create(int64_t n, int32_t k_max, int32_t dtype, const foa_dmd_opts *opts, foa_dmd_t **out) {
   if (!out) return FOA_DMD_EINVAL;
   *out = nullptr;
   if (n < 1 || dtype < 0 || dtype > 2 || k_max < 2 || k_max > max_kmax_for(dtype)) return FOA_DMD_EINVAL;
+  if (opts && (opts->reorth < 0 || opts->reorth > 2)) return FOA_DMD_EINVAL;
+  if (opts && (opts->form < 0 || opts->form > 1 || (opts->form == 1 && opts->reorth == 2))) return FOA_DMD_EINVAL;
   int sms = 0;
   int rc = check_device(&sms);
   if (rc) return rc;
@@ -496,6 +530,8 @@ extern "C" int foa_dmd_get_state(foa_dmd_t *h, int32_t *q, int32_t *stopped, dou
 extern "C" int foa_dmd_get_basis(foa_dmd_t *h, int32_t col0, int32_t ncols, void *dst_dev, int64_t ld) {
   if (!h || !dst_dev || col0 < 0 || ncols < 0 || col0 + ncols > h->kmax || ld < h->n) return FOA_DMD_EINVAL;
   if (ncols == 0) return FOA_DMD_OK;
+  const int rc = flush_pending(h);
+  if (rc) return rc;
   return cuda_status(launch_gather(h->dtype, h->V, dst_dev, ld, h->n, h->kmax, col0, ncols, h->sms, h->stream));
 }
 
@@ -538,7 +574,9 @@ uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
 
 extern "C" int foa_dmd_save(foa_dmd_t *h, const char *path) {
   if (!h || !path) return FOA_DMD_EINVAL;
-  int rc = sync_state(h, nullptr);
+  int rc = flush_pending(h);
+  if (rc) return rc;
+  rc = sync_state(h, nullptr);
   if (rc) return rc;
   const int K = h->kmax, q = h->q_host;
   const size_t s = dtype_size(h->dtype);

@@ -76,6 +76,7 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
 int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *coef, bool batch,
                   foa_dmd_push_info *info_out);
 int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_out);
+int flush_pending(foa_dmd *h);
 // eigen path (eig.cu)
 void eig_free(foa_dmd *h);
 int maybe_indicator(foa_dmd *h);  // the indicator schedule of foa_dmd_opts.indicator_every

@@ -307,6 +307,8 @@ extern "C" int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *re
   }
   const int nm = res->n_modes < o.r ? res->n_modes : o.r;
   if (nm > 0) {
+    rc = flush_pending(h);  // two-pass push: the last basis column may still be pending
+    if (rc) return rc;
     planes_kernel<<<h->sms, 256, 0, h->stream>>>(w->ysr, w->ysi, K, o.m, nm, w->yplanes);
     h->launches += 2;  // planes and the modes GEMM
     rc = launch_modes(h, o.m, w->yplanes, K, 2 * nm, res->phi_dev, res->ld_phi);

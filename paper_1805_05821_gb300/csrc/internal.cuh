@@ -20,8 +20,8 @@ constexpr int kGroup = 8;          // CTAs per first-level group of the cross-CT
 constexpr int kMaxR = 64;          // largest number of tiles in one pipeline stage
 constexpr int kMaxSlots = 8;
 
-// pass kinds
-enum PassMode : int { PASS_A = 0, PASS_B = 1, PASS_C = 2, PASS_FIRST = 3 };
+// pass kinds (PASS_B2, PASS_A2 and PASS_FIN are the two-pass push: see lag.cuh)
+enum PassMode : int { PASS_A = 0, PASS_B = 1, PASS_C = 2, PASS_FIRST = 3, PASS_B2 = 4, PASS_A2 = 5, PASS_FIN = 6 };
 
 // Device-resident state of one stream.  The host only knows an upper bound of q while pushes
 // are in flight; every kernel reads the true values here, so a launch sequence stays correct
@@ -40,8 +40,10 @@ struct DevState {
   double x_norm;     // ||x||_2 of the push in progress
   double nu;         // h_{j+1,j}
   double inv_nu;     // 1 / h_{j+1,j}
-  double pad1[3];
-  uint32_t ticket[4];// per-pass arrival counters of the last reduction level
+  int32_t pending;   // two-pass push: column pend_col is committed but not yet written to V
+  int32_t pend_col;
+  double pad1[2];
+  uint32_t ticket[8];// per-pass arrival counters of the last reduction level
   foa_dmd_push_info info;  // result of the most recent push
 };
 
@@ -51,6 +53,7 @@ struct PassArgs {
   const void *x;         // snapshot (PASS_A, PASS_FIRST), storage dtype, n elements
   void *w;               // working vector, compute dtype, ntiles*32 elements (zero beyond n)
   const double *coef;    // FP64 coefficients of the pass (beta_pre, h or s)
+  const double *coef2;   // PASS_A2 / PASS_FIN: s of the pending column
   double *partials;      // [grid][kmax+1]
   double *gpart;         // [ngroups][kmax+1]
   uint32_t *gcount;      // [ngroups]
@@ -71,11 +74,13 @@ struct PassArgs {
   int32_t reorth;
   int32_t x_aligned;     // x may be fetched with bulk copies
   int32_t batch;         // inside foa_dmd_push_batch: a failed push sets DevState::halt
-  int32_t pad;
+  int32_t form;          // 1: QR view (PASS_A projects x itself; PASS_C commits [h; nu])
   double tol;            // breakdown tolerance
   // shared-memory layout (bytes)
   int32_t slot_bytes, base_off;   // within a slot: V tiles at 0, base vector at base_off
   int32_t off_ws, off_coef, off_dot, off_comb, off_norm, off_bar, smem_total;
+  int32_t base2_off;     // PASS_A2 / PASS_FIN: w' slice within a slot
+  int32_t off_vnew, off_coef2;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -135,6 +140,15 @@ __device__ __forceinline__ int named_bar_or(int id, int count, int pred) {
       : "r"(pred), "r"(id), "r"(count)
       : "memory");
   return r;
+}
+
+// two adjacent rows of one column (8-byte or 4-byte aligned): FP32 values
+__device__ __forceinline__ float2 ld_pair(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld_pair(const __nv_bfloat16 *p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+__device__ __forceinline__ float2 ld_pair(const double *p) {
+  return make_float2(float(p[0]), float(p[1]));  // not used on the FP64 path
 }
 
 // storage -> compute conversions

@@ -5,6 +5,8 @@
 //   PASS_B      w = w - V h                     (step 11), s = V^T w         (step 12)
 //   PASS_C      w = w - V s                     (step 14), ||w||^2           (step 15)
 //   PASS_FIRST  ||x||^2 of the first snapshot (Alg. 1 step 2)
+//   PASS_B2     pass B of the two-pass push, plus ||w||^2 and the commit of h_{j+1,j} from
+//               ||w - V s||^2 = ||w||^2 - ||s||^2; the new column stays pending (lag.cuh)
 //
 // Layout and schedule.  V is row-tiled: a tile of 32 rows stores its k_max columns one after
 // another (32 contiguous elements per column), so the leading j columns of a tile are one
@@ -40,8 +42,8 @@ template <typename S, int MODE, int NC>
 __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kernel(const PassArgs a) {
   using C = typename Compute<S>::T;
   constexpr bool kFp64 = sizeof(C) == 8;
-  constexpr bool kDots = (MODE == PASS_A || MODE == PASS_B);
-  constexpr bool kNorm = (MODE == PASS_A || MODE == PASS_C || MODE == PASS_FIRST);
+  constexpr bool kDots = (MODE == PASS_A || MODE == PASS_B || MODE == PASS_B2);
+  constexpr bool kNorm = (MODE == PASS_A || MODE == PASS_C || MODE == PASS_FIRST || MODE == PASS_B2);
   constexpr bool kBaseX = (MODE == PASS_A || MODE == PASS_FIRST);
   using BaseT = typename std::conditional<kBaseX, S, C>::type;
 
@@ -64,7 +66,9 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
   uint64_t *empty = full + kMaxSlots;
   volatile int *sflag = reinterpret_cast<volatile int *>(empty + kMaxSlots);  // [0] abort [1] issued [2] last
 
-  const double cscale = (MODE == PASS_A) ? st->inv_bjj : 1.0;
+  // QR view (a.form): pass A projects x itself (w = x, no pre-vector)
+  const bool qr_a = (MODE == PASS_A) && a.form != 0;
+  const double cscale = (MODE == PASS_A && !qr_a) ? st->inv_bjj : 1.0;
   if (tid == 0) {
     for (int i = 0; i < a.slots; ++i) {
       mbar_init(&full[i], 1);
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
     sflag[2] = 0;
     mbar_fence_init();
   }
-  for (int c = tid; c < j; c += kThreads) cf[c] = static_cast<C>(a.coef[c]);
+  for (int c = tid; c < ((j + 7) & ~3); c += kThreads) cf[c] = c < j ? static_cast<C>(a.coef[c]) : C(0);
   for (int c = tid; c <= j; c += kThreads) dot[c] = 0.0;
   __syncthreads();
 
@@ -117,9 +121,10 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
   }
 
   // ------------------------------------------------------------------ consumer warps
-  C acc[kDots ? NC : 1];
+  constexpr int NACC = kFp64 ? NC : (NC + 1) / 2;
+  C acc[kDots ? NACC : 1];
 #pragma unroll
-  for (int k = 0; k < (kDots ? NC : 1); ++k) acc[k] = C(0);
+  for (int k = 0; k < (kDots ? NACC : 1); ++k) acc[k] = C(0);
   // sum of squares for the norms: compensated (Kahan) in the compute type per thread, folded into
   // FP64 once at the end
   C nsum = C(0), ncomp = C(0);
@@ -134,17 +139,33 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
 
   auto flush = [&]() {
     if constexpr (kDots) {
+      if constexpr (kFp64) {
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const int c = warp + kWarps * k;
-        if (c < j) {
-          const C v = warp_sum(acc[k]);
-          if (lane == 0) dot[c] += static_cast<double>(v);
-          acc[k] = C(0);
+        for (int k = 0; k < NC; ++k) {
+          const int c = warp + kWarps * k;
+          if (c < j) {
+            const C v = warp_sum(acc[k]);
+            if (lane == 0) dot[c] += static_cast<double>(v);
+            acc[k] = C(0);
+          }
+        }
+      } else {
+        const int half = lane >> 4;
+#pragma unroll
+        for (int kk = 0; kk < NACC; ++kk) {
+          const int c = warp + kWarps * (2 * kk + half);
+          if (warp + kWarps * (2 * kk) < j) {  // warp-uniform: at least the first half-warp's column exists
+            float v = (c < j) ? acc[kk] : 0.f;
+#pragma unroll
+            for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((lane & 15) == 0 && c < j) dot[c] += static_cast<double>(v);
+            acc[kk] = 0.f;
+          }
         }
       }
     }
   };
+
 
   for (int s = blockIdx.x; s < a.nstages; s += gridDim.x, ++it) {
     const int slot = it % a.slots;
@@ -167,110 +188,200 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
     const BaseT *bg = kBaseX ? static_cast<const BaseT *>(a.x) : static_cast<const BaseT *>(a.w);
 
     // ---------------- sweep 1: row-local part
-    const int G = (RS >= kConsumers || j == 0) ? 1 : (kConsumers / RS);
-    const int active_rows_threads = (G == 1) ? kConsumers : G * RS;
-    if (tid < active_rows_threads) {
-      const int g = (G == 1) ? 0 : tid / RS;
-      const int cpg = (j + G - 1) / G;
-      const int c0 = g * cpg;
-      const int c1 = min(j, c0 + cpg);
-      for (int row = (G == 1 ? tid : tid % RS); row < RS; row += (G == 1 ? kConsumers : RS)) {
-        const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
-        double accd = 0.0;
-        float accf = 0.f;
-        if constexpr (kFp64) {
-          double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
-          int c = c0;
-          for (; c + 4 <= c1; c += 4) {
-            b0 = fma(to_c(vr[(c + 0) * kTile]), cf[c + 0], b0);
-            b1 = fma(to_c(vr[(c + 1) * kTile]), cf[c + 1], b1);
-            b2 = fma(to_c(vr[(c + 2) * kTile]), cf[c + 2], b2);
-            b3 = fma(to_c(vr[(c + 3) * kTile]), cf[c + 3], b3);
-          }
-          for (; c < c1; ++c) b0 = fma(to_c(vr[c * kTile]), cf[c], b0);
-          accd = (b0 + b1) + (b2 + b3);
-        } else {
-          // FP32: four independent chains over the thread's columns (no FP64 in the row loop:
-          // the FP64 pipe of this part is ~1/64 of FP32)
-          float b[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) b[u] = 0.f;
-          int c = c0;
-          for (; c + 8 <= c1; c += 8) {
-            float v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = to_c(vr[(c + u) * kTile]);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) b[u] = fmaf(v[u], cf[c + u], b[u]);
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (c + u < c1) b[u] = fmaf(to_c(vr[(c + u) * kTile]), cf[c + u], b[u]);
-          accf = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
-        }
-        if (G > 1) {
-          if constexpr (kFp64) comb[g * RS + row] = accd;
-          else reinterpret_cast<float *>(comb)[g * RS + row] = accf;
-        } else {
-          // finish the row here
-          const int64_t r = r0 + row;
-          C base;
-          if (base_bulk) base = to_c(bs[row]);
-          else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
-          if constexpr (MODE == PASS_FIRST) {
-            nrm_add(base * base);
-          } else {
-            const C acc = kFp64 ? C(accd) : C(accf);
-            const C wc = (MODE == PASS_A) ? (base - acc) * C(cscale) : (base - acc);
-            static_cast<C *>(a.w)[r] = wc;
-            ws[row] = wc;
-            if constexpr (MODE == PASS_A) nrm_add(base * base);
-            else if constexpr (MODE == PASS_C) nrm_add(wc * wc);
-          }
-        }
-      }
-    }
-    if (G > 1) {
-      named_bar_sync(1, kConsumers);
-      if (tid < RS) {
-        const int row = tid;
-        C acc = C(0);
-        if constexpr (kFp64) {
-          for (int g = 0; g < G; ++g) acc += comb[g * RS + row];
-        } else {
-          const float *cb = reinterpret_cast<const float *>(comb);
-          for (int g = 0; g < G; ++g) acc += cb[g * RS + row];
-        }
-        const int64_t r = r0 + row;
-        C base;
-        if (base_bulk) base = to_c(bs[row]);
-        else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
+    auto finish_row = [&](int row, C acc) {
+      const int64_t r = r0 + row;
+      C base;
+      if (base_bulk) base = to_c(bs[row]);
+      else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
+      if constexpr (MODE == PASS_FIRST) {
+        nrm_add(base * base);
+      } else {
         const C wc = (MODE == PASS_A) ? (base - acc) * C(cscale) : (base - acc);
         static_cast<C *>(a.w)[r] = wc;
         ws[row] = wc;
         if constexpr (MODE == PASS_A) nrm_add(base * base);
-        else if constexpr (MODE == PASS_C) nrm_add(wc * wc);
+        else if constexpr (MODE == PASS_C || MODE == PASS_B2) nrm_add(wc * wc);
+      }
+    };
+    if (qr_a) {
+      for (int row = tid; row < RS; row += kConsumers) finish_row(row, C(0));
+    } else {
+      if constexpr (kFp64) {
+        const int G = (RS >= kConsumers || j == 0) ? 1 : (kConsumers / RS);
+        const int active_rows_threads = (G == 1) ? kConsumers : G * RS;
+        if (tid < active_rows_threads) {
+          const int g = (G == 1) ? 0 : tid / RS;
+          const int cpg = (j + G - 1) / G;
+          const int c0 = g * cpg;
+          const int c1 = min(j, c0 + cpg);
+          for (int row = (G == 1 ? tid : tid % RS); row < RS; row += (G == 1 ? kConsumers : RS)) {
+            const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
+            double accd = 0.0;
+            float accf = 0.f;
+            if constexpr (kFp64) {
+              double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+              int c = c0;
+              for (; c + 4 <= c1; c += 4) {
+                b0 = fma(to_c(vr[(c + 0) * kTile]), cf[c + 0], b0);
+                b1 = fma(to_c(vr[(c + 1) * kTile]), cf[c + 1], b1);
+                b2 = fma(to_c(vr[(c + 2) * kTile]), cf[c + 2], b2);
+                b3 = fma(to_c(vr[(c + 3) * kTile]), cf[c + 3], b3);
+              }
+              for (; c < c1; ++c) b0 = fma(to_c(vr[c * kTile]), cf[c], b0);
+              accd = (b0 + b1) + (b2 + b3);
+            } else {
+              // FP32: four independent chains over the thread's columns (no FP64 in the row loop:
+              // the FP64 pipe of this part is ~1/64 of FP32)
+              float b[8];
+    #pragma unroll
+              for (int u = 0; u < 8; ++u) b[u] = 0.f;
+              int c = c0;
+              for (; c + 8 <= c1; c += 8) {
+                float v[8];
+    #pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = to_c(vr[(c + u) * kTile]);
+    #pragma unroll
+                for (int u = 0; u < 8; ++u) b[u] = fmaf(v[u], cf[c + u], b[u]);
+              }
+    #pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (c + u < c1) b[u] = fmaf(to_c(vr[(c + u) * kTile]), cf[c + u], b[u]);
+              accf = ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + (b[6] + b[7]));
+            }
+            if (G > 1) {
+              if constexpr (kFp64) comb[g * RS + row] = accd;
+              else reinterpret_cast<float *>(comb)[g * RS + row] = accf;
+            } else {
+              // finish the row here
+              const int64_t r = r0 + row;
+              C base;
+              if (base_bulk) base = to_c(bs[row]);
+              else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
+              if constexpr (MODE == PASS_FIRST) {
+                nrm_add(base * base);
+              } else {
+                const C acc = kFp64 ? C(accd) : C(accf);
+                const C wc = (MODE == PASS_A) ? (base - acc) * C(cscale) : (base - acc);
+                static_cast<C *>(a.w)[r] = wc;
+                ws[row] = wc;
+                if constexpr (MODE == PASS_A) nrm_add(base * base);
+                else if constexpr (MODE == PASS_C || MODE == PASS_B2) nrm_add(wc * wc);
+              }
+            }
+          }
+        }
+        if (G > 1) {
+          named_bar_sync(1, kConsumers);
+          if (tid < RS) {
+            const int row = tid;
+            C acc = C(0);
+            if constexpr (kFp64) {
+              for (int g = 0; g < G; ++g) acc += comb[g * RS + row];
+            } else {
+              const float *cb = reinterpret_cast<const float *>(comb);
+              for (int g = 0; g < G; ++g) acc += cb[g * RS + row];
+            }
+            const int64_t r = r0 + row;
+            C base;
+            if (base_bulk) base = to_c(bs[row]);
+            else base = (r < a.n) ? C(to_c(bg[r])) : C(0);
+            const C wc = (MODE == PASS_A) ? (base - acc) * C(cscale) : (base - acc);
+            static_cast<C *>(a.w)[r] = wc;
+            ws[row] = wc;
+            if constexpr (MODE == PASS_A) nrm_add(base * base);
+            else if constexpr (MODE == PASS_C || MODE == PASS_B2) nrm_add(wc * wc);
+          }
+        }
+
+      } else {
+        // FP32 / BF16 storage: a thread owns a pair of adjacent rows (one 8-byte or 4-byte load
+        // gives both) and a group of columns; coefficients come as 16-byte broadcasts (cf is
+        // zero padded), four FP32 chains per row.
+        const int P = RS >> 1;
+        const int G1 = (P >= kConsumers || j == 0) ? 1 : (kConsumers / P);
+        float *cb = reinterpret_cast<float *>(comb);
+        if (tid < (G1 == 1 ? kConsumers : G1 * P)) {
+          const int g = (G1 == 1) ? 0 : tid / P;
+          const int cpg = (((j + G1 - 1) / G1) + 3) & ~3;
+          const int c0 = g * cpg;
+          const int c1 = min(j, c0 + cpg);
+          for (int pr = (G1 == 1 ? tid : tid % P); pr < P; pr += (G1 == 1 ? kConsumers : P)) {
+            const int row = 2 * pr;
+            const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+            int c = c0;
+            for (; c + 4 <= c1; c += 4) {
+              const float4 q = *reinterpret_cast<const float4 *>(cf + c);
+              float2 v[4];
+  #pragma unroll
+              for (int u = 0; u < 4; ++u) v[u] = ld_pair(vr + (c + u) * kTile);
+              a0[0] = fmaf(v[0].x, q.x, a0[0]); a1[0] = fmaf(v[0].y, q.x, a1[0]);
+              a0[1] = fmaf(v[1].x, q.y, a0[1]); a1[1] = fmaf(v[1].y, q.y, a1[1]);
+              a0[2] = fmaf(v[2].x, q.z, a0[2]); a1[2] = fmaf(v[2].y, q.z, a1[2]);
+              a0[3] = fmaf(v[3].x, q.w, a0[3]); a1[3] = fmaf(v[3].y, q.w, a1[3]);
+            }
+            if (c < c1) {
+              const float4 q = *reinterpret_cast<const float4 *>(cf + c);
+              float2 v[4];
+  #pragma unroll
+              for (int u = 0; u < 4; ++u) v[u] = (c + u < c1) ? ld_pair(vr + (c + u) * kTile) : make_float2(0.f, 0.f);
+              a0[0] = fmaf(v[0].x, q.x, a0[0]); a1[0] = fmaf(v[0].y, q.x, a1[0]);
+              a0[1] = fmaf(v[1].x, q.y, a0[1]); a1[1] = fmaf(v[1].y, q.y, a1[1]);
+              a0[2] = fmaf(v[2].x, q.z, a0[2]); a1[2] = fmaf(v[2].y, q.z, a1[2]);
+              a0[3] = fmaf(v[3].x, q.w, a0[3]); a1[3] = fmaf(v[3].y, q.w, a1[3]);
+            }
+            const float s0 = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+            const float s1 = (a1[0] + a1[1]) + (a1[2] + a1[3]);
+            if (G1 > 1) {
+              cb[g * RS + row] = s0;
+              cb[g * RS + row + 1] = s1;
+            } else {
+              finish_row(row, s0);
+              finish_row(row + 1, s1);
+            }
+          }
+        }
+        if (G1 > 1) {
+          named_bar_sync(1, kConsumers);
+          if (tid < RS) {
+            float acc = 0.f;
+            for (int g = 0; g < G1; ++g) acc += cb[g * RS + tid];
+            finish_row(tid, acc);
+          }
+        }
       }
     }
     named_bar_sync(1, kConsumers);  // ws complete
 
     // ---------------- sweep 2: column dot products over the staged rows
     if constexpr (kDots) {
-      for (int kt = 0; kt < nt; ++kt) {
-        const C wv = ws[kt * kTile + lane];
-        const S *vt = vs + kt * (kTile * j) + lane;
+      if constexpr (kFp64) {
+        for (int kt = 0; kt < nt; ++kt) {
+          const C wv = ws[kt * kTile + lane];
+          const S *vt = vs + kt * (kTile * j) + lane;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          const int c = warp + kWarps * k;
-          if (c < j) {
-            if constexpr (kFp64) acc[k] = fma(to_c(vt[c * kTile]), wv, acc[k]);
-            else acc[k] = fmaf(to_c(vt[c * kTile]), wv, acc[k]);
+          for (int k = 0; k < NC; ++k) {
+            const int c = warp + kWarps * k;
+            if (c < j) acc[k] = fma(to_c(vt[c * kTile]), wv, acc[k]);
           }
         }
-      }
-      if constexpr (!kFp64) {
+      } else {
+        // half-warps take alternate columns of the warp's set; a lane covers two adjacent rows
+        const int hl = lane & 15, half = lane >> 4;
+        for (int kt = 0; kt < nt; ++kt) {
+          const float2 wv = *reinterpret_cast<const float2 *>(ws + kt * kTile + 2 * hl);
+          const S *vt = vs + kt * (kTile * j) + 2 * hl;
+#pragma unroll
+          for (int kk = 0; kk < NACC; ++kk) {
+            const int c = warp + kWarps * (2 * kk + half);
+            if (c < j) {
+              const float2 v = ld_pair(vt + c * kTile);
+              acc[kk] = fmaf(v.x, wv.x, fmaf(v.y, wv.y, acc[kk]));
+            }
+          }
+        }
         since_flush += nt;
-        if (since_flush >= 32) {
+        if (since_flush >= 16) {  // 32 products per lane and column
           flush();
           since_flush = 0;
         }
@@ -343,6 +454,47 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
       a.hvec[c] = a.hvec[c] + dot[c];  // step 13: h = h + s
     }
   } else if constexpr (MODE == PASS_C) {
+    if (a.form) {
+      // QR view: beta column [h; nu]; Hbar column from beta_{:,2:} = Hbar beta (Eq. matmulhbeta) by
+      // forward substitution, Hbar_{i,j} = (h_i - beta_pre_i) / beta_jj, Hbar_{j+1,j} = nu / beta_jj
+      const double nu = sqrt(dot[j]);
+      const double xn = st->x_norm;
+      const double bjj = st->bjj;
+      int status;
+      if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
+      else if (!(nu > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
+      else status = FOA_DMD_OK;
+      const int64_t ld = a.kmax;
+      if (status != FOA_DMD_ENONFINITE)
+        for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = (a.hvec[c] - a.pre[c]) / bjj;
+      if (status == FOA_DMD_OK)
+        for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.hvec[c];
+      named_bar_sync(1, kConsumers);
+      if (tid == 0) {
+        const double hsub = nu / bjj;
+        if (status == FOA_DMD_OK) {
+          a.H[j + int64_t(j - 1) * ld] = hsub;
+          a.B[j + int64_t(j) * ld] = nu;
+          st->nu = nu;
+          st->inv_nu = 1.0 / nu;  // v_{j+1} = w / nu
+          st->q = j + 1;
+        } else if (status == FOA_DMD_EBREAKDOWN) {
+          a.H[j + int64_t(j - 1) * ld] = 0.0;
+          st->stopped = 1;
+        }
+        st->status = status;
+        if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+        foa_dmd_push_info inf;
+        inf.h_last = hsub;
+        inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+        inf.x_norm = xn;
+        inf.q = st->q;
+        inf.status = status;
+        st->info = inf;
+        if (a.info_out) *a.info_out = inf;
+      }
+      return;
+    }
     const double nu = sqrt(dot[j]);
     const double xn = st->x_norm;
     const double bjj = st->bjj;
@@ -366,6 +518,65 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
         st->nu = nu;
         st->inv_nu = 1.0 / nu;
         st->q = j + 1;
+      } else if (status == FOA_DMD_EBREAKDOWN) {
+        a.H[j + int64_t(j - 1) * ld] = 0.0;
+        st->stopped = 1;
+      }
+      st->status = status;
+      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+      foa_dmd_push_info inf;
+      inf.h_last = nu;
+      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+      inf.x_norm = xn;
+      inf.q = st->q;
+      inf.status = status;
+      st->info = inf;
+      if (a.info_out) *a.info_out = inf;
+    }
+  } else if constexpr (MODE == PASS_B2) {
+    // steps 12-13 as in PASS_B, then step 15 without a third pass: w still holds w' (after the
+    // first projection) and s = V^T w', so ||w' - V s||^2 = ||w'||^2 - ||s||^2 for orthonormal V.
+    double *ssq = nrm;  // per-thread partial sums of s_c^2, in column order within a thread
+    double t = 0.0;
+    for (int c = tid; c < j; c += kConsumers) {
+      const double sc = dot[c];
+      a.svec[c] = sc;
+      a.hvec[c] = a.hvec[c] + sc;
+      t += sc * sc;
+    }
+    ssq[tid] = t;
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      double ss = 0.0;
+      for (int i = 0; i < kConsumers; ++i) ss += ssq[i];
+      const double d = dot[j] - ss;
+      ssq[0] = d > 0.0 ? sqrt(d) : 0.0;
+    }
+    named_bar_sync(1, kConsumers);
+    const double nu = ssq[0];
+    const double xn = st->x_norm;
+    const double bjj = st->bjj;
+    int status;
+    if (!isfinite(nu) || !isfinite(xn) || !isfinite(dot[j])) status = FOA_DMD_ENONFINITE;
+    else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
+    else status = FOA_DMD_OK;
+    const int64_t ld = a.kmax;
+    if (status != FOA_DMD_ENONFINITE) {
+      for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
+    }
+    if (status == FOA_DMD_OK) {
+      for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
+    }
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      if (status == FOA_DMD_OK) {
+        a.H[j + int64_t(j - 1) * ld] = nu;
+        a.B[j + int64_t(j) * ld] = nu * bjj;
+        st->nu = nu;
+        st->inv_nu = 1.0 / nu;
+        st->q = j + 1;
+        st->pending = 1;  // v_{j+1} = (w' - V s) / nu is written by the next pass over V
+        st->pend_col = j;
       } else if (status == FOA_DMD_EBREAKDOWN) {
         a.H[j + int64_t(j - 1) * ld] = 0.0;
         st->stopped = 1;

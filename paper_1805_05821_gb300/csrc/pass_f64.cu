@@ -31,6 +31,7 @@ cudaError_t launch_pass_f64(int mode, int nc, const PassArgs &a, int grid, cudaS
   switch (mode) {
     case PASS_A: return launch_nc<PASS_A>(nc, a, grid, s);
     case PASS_B: return launch_nc<PASS_B>(nc, a, grid, s);
+    case PASS_B2: return launch_nc<PASS_B2>(nc, a, grid, s);
     case PASS_C: return launch_one<PASS_C, 8>(a, grid, s);
     default: return launch_one<PASS_FIRST, 8>(a, grid, s);
   }

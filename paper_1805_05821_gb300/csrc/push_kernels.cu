@@ -8,8 +8,10 @@ namespace foa {
 cudaError_t launch_pass_f64(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_pass_f32(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_pass_bf16(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_lag(int dtype, int mode, int nc, const PassArgs &a, int grid, cudaStream_t s);
 
 cudaError_t launch_pass(int dtype, int mode, int nc, const PassArgs &a, int grid, cudaStream_t s) {
+  if (mode == PASS_A2 || mode == PASS_FIN) return launch_lag(dtype, mode, nc, a, grid, s);
   switch (dtype) {
     case FOA_DMD_F64: return launch_pass_f64(mode, nc, a, grid, s);
     case FOA_DMD_F32: return launch_pass_f32(mode, nc, a, grid, s);

@@ -26,7 +26,8 @@ OK, EINVAL, ENOMEM, ECUDA, EFULL, EBREAKDOWN, ESTOPPED, ENONFINITE, ETIMEOUT, EI
 class foa_dmd_opts(ctypes.Structure):
     _fields_ = [("reorth", ctypes.c_int32), ("breakdown_tol", ctypes.c_double),
                 ("indicator_every", ctypes.c_int32), ("n_lead", ctypes.c_int32),
-                ("indicator_rank_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+                ("indicator_rank_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("form", ctypes.c_int32)]
 
 
 class foa_dmd_push_info(ctypes.Structure):
@@ -330,10 +331,11 @@ class FoaDMD:
     """One snapshot stream (a handle of the C ABI) with torch tensors as device buffers."""
 
     def __init__(self, n, k_max, dtype="f32", reorth=1, breakdown_tol=0.0, indicator_every=0, n_lead=32,
-                 indicator_rank_tol=0.0, stream=None, _handle=None):
+                 indicator_rank_tol=0.0, stream=None, form=0, _handle=None):
         self.n, self.k_max, self.dtype = int(n), int(k_max), dtype
         o = foa_dmd_opts_default()
         o.reorth = reorth
+        o.form = form
         o.breakdown_tol = breakdown_tol
         o.indicator_every = indicator_every
         o.n_lead = n_lead
@@ -392,10 +394,14 @@ class FoaDMD:
         return foa_dmd_save(self.h, path)
 
     @classmethod
-    def load(cls, path, dtype, n, k_max, **kw):
+    def load(cls, path, dtype, n, k_max, reorth=1, breakdown_tol=0.0, stream=None, form=0):
         o = cls.__new__(cls)
         o.n, o.k_max, o.dtype = n, k_max, dtype
         o.opts = foa_dmd_opts_default()
+        o.opts.reorth = reorth
+        o.opts.form = form
+        o.opts.breakdown_tol = breakdown_tol
+        o.opts.cuda_stream = _stream_ptr(stream)
         o.h = foa_dmd_load(path, o.opts)
         return o
 

@@ -53,6 +53,10 @@ def test_argument_checks_without_gpu(L):
     assert L.foa_dmd_create(100, 1, 1, None, ctypes.byref(h)) == foa_dmd.EINVAL
     assert L.foa_dmd_create(100, 600, 1, None, ctypes.byref(h)) == foa_dmd.EINVAL
     assert L.foa_dmd_create(100, 400, 0, None, ctypes.byref(h)) == foa_dmd.EINVAL  # FP64 limit 384
+    for bad in (-1, 3):
+        o = foa_dmd.foa_dmd_opts_default()
+        o.reorth = bad  # 0 (CGS), 1 (CGS2) and 2 (two-pass CGS2) only
+        assert L.foa_dmd_create(100, 8, 1, ctypes.byref(o), ctypes.byref(h)) == foa_dmd.EINVAL
     assert L.foa_dmd_push(None, None, None) == foa_dmd.EINVAL
     assert L.foa_dmd_eig(None, 0.0, None) == foa_dmd.EINVAL
 
