@@ -254,7 +254,8 @@ const char *foa_dmd_strerror(int status);
  * Kernel timing.  While enabled, every streaming-pass launch of the handle is bracketed by
  * CUDA events on the handle's stream.  foa_dmd_profile_read synchronises and returns, per
  * kernel kind (0: pass A = Alg. 1 steps 9-10, 1: pass B = steps 11-12, 2: pass C = steps
- * 13-15, 3: column write of step 15), the summed event time in ms, the launch count and the
+ * 13-15, 3: column write of step 15; with reorth = 2, 0 is the lagged first pass, 1 the second
+ * pass and 3 also the finishing column write), the summed event time in ms, the launch count and the
  * algorithmic bytes those launches had to move, plus the number of kernels of any kind the
  * handle launched since the previous read, then clears the counters.
  */
@@ -267,6 +268,26 @@ typedef struct {
 
 int foa_dmd_profile(foa_dmd_t *h, int enable);
 int foa_dmd_profile_read(foa_dmd_t *h, foa_dmd_kernel_stats *stats);
+
+/*
+ * Autotuner of the streaming-pass launch geometry (no counterpart in the paper).  For every pass
+ * kind the handle's options use (A/B/C, or the two passes of reorth = 2) and every j bucket up to
+ * k_max (upper ends 8, 16, 32, 64, 128, 192, 256, 320, 384, 448, 512), times each candidate
+ * (V bytes per pipeline stage 16/32/64 KB x V bytes in flight per CTA 64/96/144/192 KB x one or two
+ * CTAs per SM) on the handle's own buffers, over a prefix of V of about 2 GB, median of three
+ * launches, and keeps the fastest; later pushes of the handle launch with it.
+ *   cache_path: NULL, or a text file.  Choices found there for (device arch, dtype, floor(log2 n),
+ *               kind, bucket) are used without timing; new choices are appended.
+ *   flags:      bit 0 = time again even where the cache has a choice.
+ * The handle must hold no snapshots (q == 0, e.g. right after create or reset): tuning overwrites
+ * V, H-bar, beta and the working vector, and clears them again before returning.  Errors:
+ * EINVAL (q != 0), ENOMEM, ECUDA, ETIMEOUT.  foa_dmd_tuned_geometry reports the geometry a pass
+ * of kind (0 A, 1 B, 2 C, 3 lagged first pass, 4 second pass of the two-pass push) at basis size j
+ * launches with, and whether it was tuned (*tuned = 1) or is the default.
+ */
+int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t flags);
+int foa_dmd_tuned_geometry(foa_dmd_t *h, int32_t kind, int32_t j, int64_t *stage_bytes, int64_t *inflight_bytes,
+                           int32_t *ctas_per_sm, int32_t *tuned);
 
 /* Pinned host memory for foa_dmd_push_host (cudaHostAlloc / cudaFreeHost). */
 int foa_dmd_host_alloc(size_t bytes, void **ptr);

@@ -42,16 +42,15 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
                             : align_up(int64_t(R) * kTile * base_size, 128);
   const int64_t slot_bytes = vpart + bpart;
   const int64_t ws_bytes = align_up(2 * int64_t(R) * kTile * cs, 128);
-  const int64_t vnew_bytes = lag ? align_up(int64_t(R) * kTile * cs, 128) : 0;
+  const int64_t vnew_bytes = lag ? align_up(2 * int64_t(R) * kTile * cs, 128) : 0;  // double-buffered
   const int64_t cf_bytes = align_up(int64_t(jcap + 8) * cs, 16);
   const int64_t cf2_bytes = lag ? cf_bytes : 0;
   const int64_t comb_bytes = lag ? 2 * kConsumers * 8 : kConsumers * 8;
   const int64_t other = ws_bytes + vnew_bytes + cf_bytes + cf2_bytes + align_up(int64_t(jcap + 2) * 8, 16) +
                         comb_bytes + kConsumers * 8 + 2 * kMaxSlots * 8 + 64;
-  // two CTAs per SM for FP32/BF16 while the column accumulators fit in registers (j <= 384) and
-  // two slots fit in half the shared memory; otherwise one CTA per SM with a deeper ring
-  const int nc = pass_nc_for(jcap);
-  const bool two = (cs == 4) && (mode == PASS_C || mode == PASS_FIRST || mode == PASS_FIN || nc <= 48) &&
+  // two CTAs per SM for FP32/BF16 while two slots fit in half the shared memory; otherwise one CTA
+  // per SM with a deeper ring
+  const bool two = (cs == 4) &&
                    (2 * slot_bytes + other <= g.smem_budget2) && g.max_ctas_per_sm >= 2;
   const int64_t budget = two ? g.smem_budget2 : g.smem_budget;
   const int64_t inflight = two ? g.inflight_bytes / 2 : g.inflight_bytes;
@@ -245,7 +244,8 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
   int grid = 0;
   // with an indicator schedule one SM is left to the side-stream eigensolve
   const int sms = h->sms - (h->opts.indicator_every > 0 ? 1 : 0);
-  if (!make_pass_geom(h->geom, h->dtype, mode, jcap, h->n, h->ntiles, sms, a, grid)) return FOA_DMD_EINVAL;
+  if (!make_pass_geom(geom_for(h, mode, jcap), h->dtype, mode, jcap, h->n, h->ntiles, sms, a, grid))
+    return FOA_DMD_EINVAL;
   a.V = h->V;
   a.x = x;
   a.w = h->w;

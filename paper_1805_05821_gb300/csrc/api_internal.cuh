@@ -9,7 +9,7 @@ namespace foa {
 // Launch-geometry knobs of the streaming passes (set per handle; the autotuner may change them).
 struct Geometry {
   int64_t stage_bytes = 32 * 1024;     // target bytes of V per pipeline stage
-  int64_t smem_budget = 200 * 1024;    // shared memory of a CTA when one CTA runs per SM
+  int64_t smem_budget = 220 * 1024;    // shared memory of a CTA when one CTA runs per SM
   int64_t smem_budget2 = 112 * 1024;   // ... when two CTAs share an SM
   int64_t inflight_bytes = 96 * 1024;  // bytes of V each CTA keeps in flight
   int max_ctas_per_sm = 2;
@@ -22,6 +22,9 @@ struct EventPair {
 };
 
 struct EigWork;  // device workspace of the eigensolver (eig.cu)
+
+constexpr int kTuneKinds = 5;     // pass kinds with their own tuned geometry: A, B, C, A2, B2
+constexpr int kTuneBuckets = 11;  // j buckets (upper ends 8, 16, 32, 64, 128, 192, ..., 512)
 
 }  // namespace foa
 
@@ -36,6 +39,8 @@ struct foa_dmd {
   cudaStream_t stream = nullptr;
   double tol = 0.0;
   foa::Geometry geom;
+  foa::Geometry tuned[foa::kTuneKinds][foa::kTuneBuckets];  // foa_dmd_autotune's choices
+  bool tuned_ok[foa::kTuneKinds][foa::kTuneBuckets] = {};
   void *V = nullptr;
   void *w = nullptr;
   double *H = nullptr, *B = nullptr, *pre = nullptr, *hvec = nullptr, *svec = nullptr;
@@ -77,6 +82,9 @@ int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *c
                   foa_dmd_push_info *info_out);
 int enqueue_push(foa_dmd *h, const void *x, bool batch, foa_dmd_push_info *info_out);
 int flush_pending(foa_dmd *h);
+// geometry of a pass launch: the tuned choice for (kind, j bucket) if any, else the handle default
+const Geometry &geom_for(const foa_dmd *h, int mode, int jcap);
+int tune_bucket(int j);
 // eigen path (eig.cu)
 void eig_free(foa_dmd *h);
 int maybe_indicator(foa_dmd *h);  // the indicator schedule of foa_dmd_opts.indicator_every

@@ -1,5 +1,6 @@
 // Instantiations and launcher of the lagged first pass of the two-pass push (lag.cuh).
 #include "lag.cuh"
+#include "lag_ws.cuh"
 
 namespace foa {
 
@@ -16,9 +17,32 @@ static cudaError_t launch_lag_one(const PassArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename S, int NC>
+static cudaError_t launch_lag_ws_one(const PassArgs &a, int grid, cudaStream_t s) {
+  auto k = lag_ws_kernel<S, NC>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k<<<grid, kThreads, a.smem_total, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename S>
 static cudaError_t launch_lag_t(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s) {
   if (mode == PASS_FIN) return launch_lag_one<S, 8, true>(a, grid, s);
+  if constexpr (sizeof(typename Compute<S>::T) == 4) {
+    // FP32/BF16: the warp-specialised kernel (row and column sweeps on different warps)
+    switch (nc) {
+      case 8: return launch_lag_ws_one<S, 8>(a, grid, s);
+      case 16: return launch_lag_ws_one<S, 16>(a, grid, s);
+      case 32: return launch_lag_ws_one<S, 32>(a, grid, s);
+      case 48: return launch_lag_ws_one<S, 48>(a, grid, s);
+      default: return launch_lag_ws_one<S, 64>(a, grid, s);
+    }
+  }
   switch (nc) {
     case 8: return launch_lag_one<S, 8, false>(a, grid, s);
     case 16: return launch_lag_one<S, 16, false>(a, grid, s);

@@ -31,6 +31,245 @@
 
 namespace foa {
 
+// Cross-CTA reduction and the scalar part of the step, shared by the streaming-pass kernels.
+// On entry every consumer thread (tid < kConsumers) has added its column partials into dot[0..j)
+// and stored its norm partial in nrm[tid]; dot[j] receives the CTA's norm.  Each CTA leaves its
+// FP64 partial vector in global memory; the last CTA of every group of 8 CTAs (atomic ticket)
+// sums its group in CTA order, and the last group sums the group partials in group order, so the
+// reduction is deterministic.  That last CTA then applies the scalar part of the step.
+template <int MODE>
+__device__ __forceinline__ void pass_epilogue(const PassArgs &a, DevState *st, double *dot, double *nrm,
+                                              volatile int *sflag, const int j, const int tid) {
+  constexpr bool kNorm = (MODE == PASS_A || MODE == PASS_C || MODE == PASS_FIRST || MODE == PASS_B2);
+  named_bar_sync(1, kConsumers);
+  const int len = j + 1;
+  if (tid == 0) {
+    if constexpr (kNorm) {
+      double t = 0.0;
+      for (int i = 0; i < kConsumers; ++i) t += nrm[i];
+      dot[j] = t;
+    }
+  }
+  named_bar_sync(1, kConsumers);
+  double *mypart = a.partials + size_t(blockIdx.x) * (a.kmax + 1);
+  for (int c = tid; c < len; c += kConsumers) mypart[c] = dot[c];
+  __threadfence();
+  named_bar_sync(1, kConsumers);
+
+  // ---------------- two-level deterministic reduction (last arriving CTA of each group)
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  const int grp = blockIdx.x / kGroup;
+  const int gfirst = grp * kGroup;
+  const int gsize = min(kGroup, int(gridDim.x) - gfirst);
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&a.gcount[grp], 1u);
+    sflag[2] = (t == unsigned(gsize - 1)) ? 1 : 0;
+  }
+  named_bar_sync(1, kConsumers);
+  if (!sflag[2]) return;
+  __threadfence();
+  double *gp = a.gpart + size_t(grp) * (a.kmax + 1);
+  for (int c = tid; c < len; c += kConsumers) {
+    double t = 0.0;
+    for (int b = 0; b < gsize; ++b) t += __ldcg(a.partials + size_t(gfirst + b) * (a.kmax + 1) + c);
+    gp[c] = t;
+  }
+  __threadfence();
+  named_bar_sync(1, kConsumers);
+  if (tid == 0) {
+    a.gcount[grp] = 0u;
+    const unsigned t = atomicAdd(&st->ticket[MODE], 1u);
+    sflag[2] = (t == unsigned(ngroups - 1)) ? 1 : 0;
+  }
+  named_bar_sync(1, kConsumers);
+  if (!sflag[2]) return;
+  __threadfence();
+  for (int c = tid; c < len; c += kConsumers) {
+    double t = 0.0;
+    for (int g = 0; g < ngroups; ++g) t += __ldcg(a.gpart + size_t(g) * (a.kmax + 1) + c);
+    dot[c] = t;
+  }
+  if (tid == 0) st->ticket[MODE] = 0u;
+  named_bar_sync(1, kConsumers);
+
+  // ---------------- scalar part of the step (one CTA)
+  if constexpr (MODE == PASS_A) {
+    for (int c = tid; c < j; c += kConsumers) a.hvec[c] = dot[c];
+    if (tid == 0) st->x_norm = sqrt(dot[j]);
+  } else if constexpr (MODE == PASS_B) {
+    for (int c = tid; c < j; c += kConsumers) {
+      a.svec[c] = dot[c];
+      a.hvec[c] = a.hvec[c] + dot[c];  // step 13: h = h + s
+    }
+  } else if constexpr (MODE == PASS_C) {
+    if (a.form) {
+      // QR view: beta column [h; nu]; Hbar column from beta_{:,2:} = Hbar beta (Eq. matmulhbeta) by
+      // forward substitution, Hbar_{i,j} = (h_i - beta_pre_i) / beta_jj, Hbar_{j+1,j} = nu / beta_jj
+      const double nu = sqrt(dot[j]);
+      const double xn = st->x_norm;
+      const double bjj = st->bjj;
+      int status;
+      if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
+      else if (!(nu > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
+      else status = FOA_DMD_OK;
+      const int64_t ld = a.kmax;
+      if (status != FOA_DMD_ENONFINITE)
+        for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = (a.hvec[c] - a.pre[c]) / bjj;
+      if (status == FOA_DMD_OK)
+        for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.hvec[c];
+      named_bar_sync(1, kConsumers);
+      if (tid == 0) {
+        const double hsub = nu / bjj;
+        if (status == FOA_DMD_OK) {
+          a.H[j + int64_t(j - 1) * ld] = hsub;
+          a.B[j + int64_t(j) * ld] = nu;
+          st->nu = nu;
+          st->inv_nu = 1.0 / nu;  // v_{j+1} = w / nu
+          st->q = j + 1;
+        } else if (status == FOA_DMD_EBREAKDOWN) {
+          a.H[j + int64_t(j - 1) * ld] = 0.0;
+          st->stopped = 1;
+        }
+        st->status = status;
+        if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+        foa_dmd_push_info inf;
+        inf.h_last = hsub;
+        inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+        inf.x_norm = xn;
+        inf.q = st->q;
+        inf.status = status;
+        st->info = inf;
+        if (a.info_out) *a.info_out = inf;
+      }
+      return;
+    }
+    const double nu = sqrt(dot[j]);
+    const double xn = st->x_norm;
+    const double bjj = st->bjj;
+    int status;
+    if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
+    else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
+    else status = FOA_DMD_OK;
+    const int64_t ld = a.kmax;
+    if (status != FOA_DMD_ENONFINITE) {
+      for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
+    }
+    if (status == FOA_DMD_OK) {
+      // steps 16-18: beta_{i,j+1} = beta_pre_i + h_{i,j} beta_{j,j}; beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}
+      for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
+    }
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      if (status == FOA_DMD_OK) {
+        a.H[j + int64_t(j - 1) * ld] = nu;
+        a.B[j + int64_t(j) * ld] = nu * bjj;
+        st->nu = nu;
+        st->inv_nu = 1.0 / nu;
+        st->q = j + 1;
+      } else if (status == FOA_DMD_EBREAKDOWN) {
+        a.H[j + int64_t(j - 1) * ld] = 0.0;
+        st->stopped = 1;
+      }
+      st->status = status;
+      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+      foa_dmd_push_info inf;
+      inf.h_last = nu;
+      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+      inf.x_norm = xn;
+      inf.q = st->q;
+      inf.status = status;
+      st->info = inf;
+      if (a.info_out) *a.info_out = inf;
+    }
+  } else if constexpr (MODE == PASS_B2) {
+    // steps 12-13 as in PASS_B, then step 15 without a third pass: w still holds w' (after the
+    // first projection) and s = V^T w', so ||w' - V s||^2 = ||w'||^2 - ||s||^2 for orthonormal V.
+    double *ssq = nrm;  // per-thread partial sums of s_c^2, in column order within a thread
+    double t = 0.0;
+    for (int c = tid; c < j; c += kConsumers) {
+      const double sc = dot[c];
+      a.svec[c] = sc;
+      a.hvec[c] = a.hvec[c] + sc;
+      t += sc * sc;
+    }
+    ssq[tid] = t;
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      double ss = 0.0;
+      for (int i = 0; i < kConsumers; ++i) ss += ssq[i];
+      const double d = dot[j] - ss;
+      ssq[0] = d > 0.0 ? sqrt(d) : 0.0;
+    }
+    named_bar_sync(1, kConsumers);
+    const double nu = ssq[0];
+    const double xn = st->x_norm;
+    const double bjj = st->bjj;
+    int status;
+    if (!isfinite(nu) || !isfinite(xn) || !isfinite(dot[j])) status = FOA_DMD_ENONFINITE;
+    else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
+    else status = FOA_DMD_OK;
+    const int64_t ld = a.kmax;
+    if (status != FOA_DMD_ENONFINITE) {
+      for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
+    }
+    if (status == FOA_DMD_OK) {
+      for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
+    }
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      if (status == FOA_DMD_OK) {
+        a.H[j + int64_t(j - 1) * ld] = nu;
+        a.B[j + int64_t(j) * ld] = nu * bjj;
+        st->nu = nu;
+        st->inv_nu = 1.0 / nu;
+        st->q = j + 1;
+        st->pending = 1;  // v_{j+1} = (w' - V s) / nu is written by the next pass over V
+        st->pend_col = j;
+      } else if (status == FOA_DMD_EBREAKDOWN) {
+        a.H[j + int64_t(j - 1) * ld] = 0.0;
+        st->stopped = 1;
+      }
+      st->status = status;
+      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+      foa_dmd_push_info inf;
+      inf.h_last = nu;
+      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+      inf.x_norm = xn;
+      inf.q = st->q;
+      inf.status = status;
+      st->info = inf;
+      if (a.info_out) *a.info_out = inf;
+    }
+  } else if constexpr (MODE == PASS_FIRST) {
+    if (tid == 0) {
+      const double b = sqrt(dot[0]);
+      int status;
+      if (!isfinite(b)) status = FOA_DMD_ENONFINITE;
+      else if (!(b > 0.0)) status = FOA_DMD_EBREAKDOWN;
+      else status = FOA_DMD_OK;
+      if (status == FOA_DMD_OK) {
+        a.B[0] = b;  // Alg. 1 step 3
+        st->nu = b;
+        st->inv_nu = 1.0 / b;
+        st->q = 1;
+      } else if (status == FOA_DMD_EBREAKDOWN) {
+        st->stopped = 1;
+      }
+      st->x_norm = b;
+      st->status = status;
+      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
+      foa_dmd_push_info inf;
+      inf.h_last = b;
+      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
+      inf.x_norm = b;
+      inf.q = st->q;
+      inf.status = status;
+      st->info = inf;
+      if (a.info_out) *a.info_out = inf;
+    }
+  }
+}
+
 // Two CTAs per SM for the FP32/BF16 forms while the column accumulators fit (NC <= 48, i.e.
 // j <= 384): one CTA's barrier phases then overlap the other's compute.
 template <typename S, int NC>
@@ -392,234 +631,8 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
     if (lane == 0) mbar_arrive(&empty[slot]);
   }
   flush();
-  if constexpr (kNorm) nrm[tid] = double(nsum) - double(ncomp);
-  named_bar_sync(1, kConsumers);
-  const int len = j + 1;
-  if (tid == 0) {
-    if constexpr (kNorm) {
-      double t = 0.0;
-      for (int i = 0; i < kConsumers; ++i) t += nrm[i];
-      dot[j] = t;
-    }
-  }
-  named_bar_sync(1, kConsumers);
-  double *mypart = a.partials + size_t(blockIdx.x) * (a.kmax + 1);
-  for (int c = tid; c < len; c += kConsumers) mypart[c] = dot[c];
-  __threadfence();
-  named_bar_sync(1, kConsumers);
-
-  // ---------------- two-level deterministic reduction (last arriving CTA of each group)
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
-  const int grp = blockIdx.x / kGroup;
-  const int gfirst = grp * kGroup;
-  const int gsize = min(kGroup, int(gridDim.x) - gfirst);
-  if (tid == 0) {
-    const unsigned t = atomicAdd(&a.gcount[grp], 1u);
-    sflag[2] = (t == unsigned(gsize - 1)) ? 1 : 0;
-  }
-  named_bar_sync(1, kConsumers);
-  if (!sflag[2]) return;
-  __threadfence();
-  double *gp = a.gpart + size_t(grp) * (a.kmax + 1);
-  for (int c = tid; c < len; c += kConsumers) {
-    double t = 0.0;
-    for (int b = 0; b < gsize; ++b) t += __ldcg(a.partials + size_t(gfirst + b) * (a.kmax + 1) + c);
-    gp[c] = t;
-  }
-  __threadfence();
-  named_bar_sync(1, kConsumers);
-  if (tid == 0) {
-    a.gcount[grp] = 0u;
-    const unsigned t = atomicAdd(&st->ticket[MODE], 1u);
-    sflag[2] = (t == unsigned(ngroups - 1)) ? 1 : 0;
-  }
-  named_bar_sync(1, kConsumers);
-  if (!sflag[2]) return;
-  __threadfence();
-  for (int c = tid; c < len; c += kConsumers) {
-    double t = 0.0;
-    for (int g = 0; g < ngroups; ++g) t += __ldcg(a.gpart + size_t(g) * (a.kmax + 1) + c);
-    dot[c] = t;
-  }
-  if (tid == 0) st->ticket[MODE] = 0u;
-  named_bar_sync(1, kConsumers);
-
-  // ---------------- scalar part of the step (one CTA)
-  if constexpr (MODE == PASS_A) {
-    for (int c = tid; c < j; c += kConsumers) a.hvec[c] = dot[c];
-    if (tid == 0) st->x_norm = sqrt(dot[j]);
-  } else if constexpr (MODE == PASS_B) {
-    for (int c = tid; c < j; c += kConsumers) {
-      a.svec[c] = dot[c];
-      a.hvec[c] = a.hvec[c] + dot[c];  // step 13: h = h + s
-    }
-  } else if constexpr (MODE == PASS_C) {
-    if (a.form) {
-      // QR view: beta column [h; nu]; Hbar column from beta_{:,2:} = Hbar beta (Eq. matmulhbeta) by
-      // forward substitution, Hbar_{i,j} = (h_i - beta_pre_i) / beta_jj, Hbar_{j+1,j} = nu / beta_jj
-      const double nu = sqrt(dot[j]);
-      const double xn = st->x_norm;
-      const double bjj = st->bjj;
-      int status;
-      if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
-      else if (!(nu > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
-      else status = FOA_DMD_OK;
-      const int64_t ld = a.kmax;
-      if (status != FOA_DMD_ENONFINITE)
-        for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = (a.hvec[c] - a.pre[c]) / bjj;
-      if (status == FOA_DMD_OK)
-        for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.hvec[c];
-      named_bar_sync(1, kConsumers);
-      if (tid == 0) {
-        const double hsub = nu / bjj;
-        if (status == FOA_DMD_OK) {
-          a.H[j + int64_t(j - 1) * ld] = hsub;
-          a.B[j + int64_t(j) * ld] = nu;
-          st->nu = nu;
-          st->inv_nu = 1.0 / nu;  // v_{j+1} = w / nu
-          st->q = j + 1;
-        } else if (status == FOA_DMD_EBREAKDOWN) {
-          a.H[j + int64_t(j - 1) * ld] = 0.0;
-          st->stopped = 1;
-        }
-        st->status = status;
-        if (status != FOA_DMD_OK && a.batch) st->halt = 1;
-        foa_dmd_push_info inf;
-        inf.h_last = hsub;
-        inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
-        inf.x_norm = xn;
-        inf.q = st->q;
-        inf.status = status;
-        st->info = inf;
-        if (a.info_out) *a.info_out = inf;
-      }
-      return;
-    }
-    const double nu = sqrt(dot[j]);
-    const double xn = st->x_norm;
-    const double bjj = st->bjj;
-    int status;
-    if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
-    else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
-    else status = FOA_DMD_OK;
-    const int64_t ld = a.kmax;
-    if (status != FOA_DMD_ENONFINITE) {
-      for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
-    }
-    if (status == FOA_DMD_OK) {
-      // steps 16-18: beta_{i,j+1} = beta_pre_i + h_{i,j} beta_{j,j}; beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}
-      for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
-    }
-    named_bar_sync(1, kConsumers);
-    if (tid == 0) {
-      if (status == FOA_DMD_OK) {
-        a.H[j + int64_t(j - 1) * ld] = nu;
-        a.B[j + int64_t(j) * ld] = nu * bjj;
-        st->nu = nu;
-        st->inv_nu = 1.0 / nu;
-        st->q = j + 1;
-      } else if (status == FOA_DMD_EBREAKDOWN) {
-        a.H[j + int64_t(j - 1) * ld] = 0.0;
-        st->stopped = 1;
-      }
-      st->status = status;
-      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
-      foa_dmd_push_info inf;
-      inf.h_last = nu;
-      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
-      inf.x_norm = xn;
-      inf.q = st->q;
-      inf.status = status;
-      st->info = inf;
-      if (a.info_out) *a.info_out = inf;
-    }
-  } else if constexpr (MODE == PASS_B2) {
-    // steps 12-13 as in PASS_B, then step 15 without a third pass: w still holds w' (after the
-    // first projection) and s = V^T w', so ||w' - V s||^2 = ||w'||^2 - ||s||^2 for orthonormal V.
-    double *ssq = nrm;  // per-thread partial sums of s_c^2, in column order within a thread
-    double t = 0.0;
-    for (int c = tid; c < j; c += kConsumers) {
-      const double sc = dot[c];
-      a.svec[c] = sc;
-      a.hvec[c] = a.hvec[c] + sc;
-      t += sc * sc;
-    }
-    ssq[tid] = t;
-    named_bar_sync(1, kConsumers);
-    if (tid == 0) {
-      double ss = 0.0;
-      for (int i = 0; i < kConsumers; ++i) ss += ssq[i];
-      const double d = dot[j] - ss;
-      ssq[0] = d > 0.0 ? sqrt(d) : 0.0;
-    }
-    named_bar_sync(1, kConsumers);
-    const double nu = ssq[0];
-    const double xn = st->x_norm;
-    const double bjj = st->bjj;
-    int status;
-    if (!isfinite(nu) || !isfinite(xn) || !isfinite(dot[j])) status = FOA_DMD_ENONFINITE;
-    else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
-    else status = FOA_DMD_OK;
-    const int64_t ld = a.kmax;
-    if (status != FOA_DMD_ENONFINITE) {
-      for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
-    }
-    if (status == FOA_DMD_OK) {
-      for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
-    }
-    named_bar_sync(1, kConsumers);
-    if (tid == 0) {
-      if (status == FOA_DMD_OK) {
-        a.H[j + int64_t(j - 1) * ld] = nu;
-        a.B[j + int64_t(j) * ld] = nu * bjj;
-        st->nu = nu;
-        st->inv_nu = 1.0 / nu;
-        st->q = j + 1;
-        st->pending = 1;  // v_{j+1} = (w' - V s) / nu is written by the next pass over V
-        st->pend_col = j;
-      } else if (status == FOA_DMD_EBREAKDOWN) {
-        a.H[j + int64_t(j - 1) * ld] = 0.0;
-        st->stopped = 1;
-      }
-      st->status = status;
-      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
-      foa_dmd_push_info inf;
-      inf.h_last = nu;
-      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
-      inf.x_norm = xn;
-      inf.q = st->q;
-      inf.status = status;
-      st->info = inf;
-      if (a.info_out) *a.info_out = inf;
-    }
-  } else if constexpr (MODE == PASS_FIRST) {
-    if (tid == 0) {
-      const double b = sqrt(dot[0]);
-      int status;
-      if (!isfinite(b)) status = FOA_DMD_ENONFINITE;
-      else if (!(b > 0.0)) status = FOA_DMD_EBREAKDOWN;
-      else status = FOA_DMD_OK;
-      if (status == FOA_DMD_OK) {
-        a.B[0] = b;  // Alg. 1 step 3
-        st->nu = b;
-        st->inv_nu = 1.0 / b;
-        st->q = 1;
-      } else if (status == FOA_DMD_EBREAKDOWN) {
-        st->stopped = 1;
-      }
-      st->x_norm = b;
-      st->status = status;
-      if (status != FOA_DMD_OK && a.batch) st->halt = 1;
-      foa_dmd_push_info inf;
-      inf.h_last = b;
-      inf.indicator = __longlong_as_double(0x7ff8000000000000ll);
-      inf.x_norm = b;
-      inf.q = st->q;
-      inf.status = status;
-      st->info = inf;
-      if (a.info_out) *a.info_out = inf;
-    }
-  }
+  nrm[tid] = kNorm ? double(nsum) - double(ncomp) : 0.0;
+  pass_epilogue<MODE>(a, st, dot, nrm, sflag, j, tid);
 }
 
 }  // namespace foa

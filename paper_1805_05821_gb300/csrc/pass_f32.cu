@@ -1,5 +1,6 @@
 // Instantiations of the streaming-pass kernel for float storage.
 #include "pass.cuh"
+#include "pass_ws.cuh"
 
 namespace foa {
 
@@ -16,6 +17,31 @@ static cudaError_t launch_one(const PassArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// passes with column dots: the warp-specialised kernel
+template <int MODE, int NC>
+static cudaError_t launch_ws_one(const PassArgs &a, int grid, cudaStream_t s) {
+  auto k = pass_ws_kernel<float, MODE, NC>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k<<<grid, kThreads, a.smem_total, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_ws(int nc, const PassArgs &a, int grid, cudaStream_t s) {
+  switch (nc) {
+    case 8: return launch_ws_one<MODE, 8>(a, grid, s);
+    case 16: return launch_ws_one<MODE, 16>(a, grid, s);
+    case 32: return launch_ws_one<MODE, 32>(a, grid, s);
+    case 48: return launch_ws_one<MODE, 48>(a, grid, s);
+    default: return launch_ws_one<MODE, 64>(a, grid, s);
+  }
+}
+
 template <int MODE>
 static cudaError_t launch_nc(int nc, const PassArgs &a, int grid, cudaStream_t s) {
   switch (nc) {
@@ -29,9 +55,9 @@ static cudaError_t launch_nc(int nc, const PassArgs &a, int grid, cudaStream_t s
 
 cudaError_t launch_pass_f32(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s) {
   switch (mode) {
-    case PASS_A: return launch_nc<PASS_A>(nc, a, grid, s);
-    case PASS_B: return launch_nc<PASS_B>(nc, a, grid, s);
-    case PASS_B2: return launch_nc<PASS_B2>(nc, a, grid, s);
+    case PASS_A: return launch_ws<PASS_A>(nc, a, grid, s);
+    case PASS_B: return launch_ws<PASS_B>(nc, a, grid, s);
+    case PASS_B2: return launch_ws<PASS_B2>(nc, a, grid, s);
     case PASS_C: return launch_one<PASS_C, 8>(a, grid, s);
     default: return launch_one<PASS_FIRST, 8>(a, grid, s);
   }

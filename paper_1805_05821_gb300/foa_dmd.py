@@ -86,6 +86,9 @@ def lib():
             "foa_dmd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
             "foa_dmd_profile": (ctypes.c_int, [vp, ctypes.c_int]),
             "foa_dmd_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(foa_dmd_kernel_stats)]),
+            "foa_dmd_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32]),
+            "foa_dmd_tuned_geometry": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                                      ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "foa_dmd_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(vp)]),
             "foa_dmd_host_free": (ctypes.c_int, [vp]),
             "foa_dmd_batch_create": (ctypes.c_int, [i32, ctypes.POINTER(i64), ctypes.POINTER(i32), i32,
@@ -270,6 +273,19 @@ def foa_dmd_profile_read(h):
             "total_launches": int(s.total_launches)}
 
 
+def foa_dmd_autotune(h, cache_path=None, force=False):
+    path = str(cache_path).encode() if cache_path else None
+    return _check(lib().foa_dmd_autotune(h, path, 1 if force else 0), "foa_dmd_autotune")
+
+
+def foa_dmd_tuned_geometry(h, kind, j):
+    st, inf = ctypes.c_int64(), ctypes.c_int64()
+    ctas, tuned = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().foa_dmd_tuned_geometry(h, int(kind), int(j), ctypes.byref(st), ctypes.byref(inf), ctypes.byref(ctas),
+                                        ctypes.byref(tuned)), "foa_dmd_tuned_geometry")
+    return {"stage_bytes": st.value, "inflight_bytes": inf.value, "ctas_per_sm": ctas.value, "tuned": bool(tuned.value)}
+
+
 def foa_dmd_host_alloc(nbytes):
     p = ctypes.c_void_p()
     _check(lib().foa_dmd_host_alloc(int(nbytes), ctypes.byref(p)), "foa_dmd_host_alloc")
@@ -404,6 +420,12 @@ class FoaDMD:
         o.opts.cuda_stream = _stream_ptr(stream)
         o.h = foa_dmd_load(path, o.opts)
         return o
+
+    def autotune(self, cache_path=None, force=False):
+        return foa_dmd_autotune(self.h, cache_path, force)
+
+    def tuned_geometry(self, kind, j):
+        return foa_dmd_tuned_geometry(self.h, kind, j)
 
     def profile(self, enable=True):
         foa_dmd_profile(self.h, enable)
