@@ -6,10 +6,12 @@ geometry.  The FP64 oracle cannot hold this size (V alone would be 206 GB), so t
 checked through properties that hold at any size, on sampled outputs the host recomputes one
 by one (the device generator is bit-identical to the host rows):
   * X = V beta (Sec. 3.1, Eq. qrfactbstab): every snapshot on 2048 sampled rows, normwise
-    ||x_t - V beta_t|| <= 1e-4 ||x_t|| (384 u_fp32 with room);
-  * V^T V = I (Eq. qrfactorth) on the diagonal 64-column blocks, in FP64, to 1e-5;
+    ||X - V beta|| <= 2e-6 ||X|| (about 32 u_fp32; measured 8.9e-8);
+  * V^T V = I (Eq. qrfactorth) on the diagonal 64-column blocks, in FP64, max entry 2e-6
+    (measured 1.2e-7);
   * beta upper triangular with a positive diagonal, H-bar upper Hessenberg;
-  * the leading 32 Ritz values against the planted eigenvalues e^{sigma +- i omega}, 1e-6.
+  * the leading 32 Ritz values against the planted eigenvalues e^{sigma +- i omega}, relative
+    1e-7 (measured 1.2e-9).
 """
 import numpy as np
 import pytest
@@ -66,7 +68,8 @@ def test_fields4x256_full_size_properties():
             G += C @ C.T
             del C
         E = (G - torch.eye(nc, dtype=torch.float64, device="cuda")).abs().max().item()
-        assert E <= 1e-5, (c0, E)
+        print(f"orthogonality block {c0}: max|VtV - I| = {E:.3e}")
+        assert E <= 2e-6, (c0, E)
         del Vb, G
     torch.cuda.empty_cache()
     num = den = 0.0
@@ -75,7 +78,8 @@ def test_fields4x256_full_size_properties():
         r = xt - Vs @ B[:q, t]
         num += float(r @ r)
         den += float(xt @ xt)
-    assert np.sqrt(num / den) <= 1e-4, np.sqrt(num / den)
+    print(f"sampled ||X - V beta|| / ||X|| = {np.sqrt(num / den):.3e}")
+    assert np.sqrt(num / den) <= 2e-6, np.sqrt(num / den)
 
     # leading Ritz values against the planted eigenvalues
     res = g.eig(rank_tol=-1.0)
@@ -84,7 +88,8 @@ def test_fields4x256_full_size_properties():
     D = np.abs(lead[:, None] - spec.lam[None, :])
     from scipy.optimize import linear_sum_assignment
     ri, ci = linear_sum_assignment(D)
-    assert np.max(D[ri, ci] / np.abs(spec.lam[ci])) <= 1e-6
+    print(f"leading 32 Ritz values vs planted: max rel err {np.max(D[ri, ci] / np.abs(spec.lam[ci])):.3e}")
+    assert np.max(D[ri, ci] / np.abs(spec.lam[ci])) <= 1e-7
     g.close()
     del buf, tabs, coefs
     torch.cuda.empty_cache()
