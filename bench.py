@@ -325,8 +325,8 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None,
             "traffic": (ratio * pass_bytes / pass_launches) if (ratio and pass_launches) else None,
-            "kernel": ("pass_kernel (streaming passes A/B/C over V)" if args.reorth == 1 else
-                       "lag_kernel + pass_kernel (the two streaming passes over V)"),
+            "kernel": ("streaming passes over V: pass_ws_kernel (A, B) + pass_kernel (C)" if args.reorth == 1 else
+                       "streaming passes over V: lag_ws_kernel (A2) + pass_ws_kernel (B2)"),
             "algorithmic_bytes_per_launch": pass_bytes / pass_launches if pass_launches else None,
             "avg_launch_ms": pass_ms / pass_launches if pass_launches else None,
             "share_of_step": pass_ms / (secs * 1e3) if secs > 0 else None,
