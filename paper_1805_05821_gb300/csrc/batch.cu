@@ -4,13 +4,17 @@
 // plan_kernel (1 CTA) reads every stream's device state and the caller's pointer array and
 // builds the work list: phase 0 = beta_pre of each active stream (Alg. 1 steps 5-8), phases
 // 1-3 = the streaming passes A, B, C (steps 9-15) cut into chunks of whole pipeline stages,
-// phase 4 = the append of the new basis vector (step 15).  The persistent kernel takes items
-// from one global counter in list order.  An item of phase p of stream s waits (bounded) until
-// stream s has finished phase p-1; because every item of phase p-1 precedes it in the list and
-// all CTAs are co-resident, that wait always ends.  The last finisher of a (stream, phase) sums
-// the chunk partials in chunk order (deterministic) and applies the scalar part of the step.
-// Stage processing matches the single-stream pass kernel: bulk async copies of whole row tiles
-// into a shared-memory double buffer, a row-local sweep and a column sweep per stage.
+// phase 4 = the append of the new basis vector (step 15).  Items are taken from one global
+// counter in list order (phase-major).  An item of phase p of stream s starts once stream s has
+// finished phase p-1 (bounded wait); every item of phase p-1 precedes it in the list and all CTAs
+// are co-resident, so that wait always ends.  The last finisher of a (stream, phase) sums the
+// chunk partials in chunk order (deterministic) and applies the scalar part of the step.
+//
+// Inside a CTA the roles are those of the single-stream warp-specialised pass: warp 8 fetches
+// items, waits for their dependencies, publishes them to the consumers through a two-deep item
+// ring and streams their stages into a shared-memory slot ring with bulk async copies; warps 0-3
+// make the row-local sweep of each stage, warps 4-7 the column dots of the previous one.  The
+// producer runs ahead into the next item while the consumers finish the current one.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -21,13 +25,11 @@
 namespace foa {
 namespace bt {
 
-constexpr int THREADS = 256;
-constexpr int SLOT_V = 64 * 1024;     // V bytes per stage slot (one 32-row tile at k_max = 512, FP32)
-constexpr int SLOT_B = 8 * 1024;      // base vector bytes per slot
-constexpr int SLOTS = 2;
-constexpr int MAX_R = 64;
-constexpr int64_t CHUNK_BYTES = 16ll << 20;  // V bytes per work item
-constexpr int NC = 64;                // column accumulators per warp (k_max <= 512)
+constexpr int MAX_R = 64;             // tiles per stage
+constexpr int SLOT_B = MAX_R * 32 * 4;  // base-vector bytes per slot (x or w of one stage)
+constexpr int MAX_SLOTS = 4;
+constexpr int NCB = 64;               // column accumulators per column-group lane (k_max <= 512)
+constexpr int ROW_WARPS = 4, COL_WARPS = 4, ROW_THREADS = ROW_WARPS * 32;
 
 struct StreamDesc {
   int64_t n;
@@ -70,6 +72,9 @@ struct BatchArgs {
   double tol;
   int32_t S;
   int32_t *err;        // sticky
+  int32_t slot_v;      // V bytes per stage slot (a whole tile of the widest stream fits)
+  int32_t nslots;      // slot ring depth
+  int64_t chunk_bytes; // V bytes per work item
 };
 
 template <typename S>
@@ -98,13 +103,13 @@ __global__ void plan_kernel(BatchArgs a, int ssize) {
     int R = MAX_R;
     if (j > 0) {
       R = 1;
-      while (R * 2 <= MAX_R && int64_t(R * 2) * tb <= SLOT_V) R *= 2;
+      while (R * 2 <= MAX_R && int64_t(R * 2) * tb <= a.slot_v) R *= 2;
     }
     Plan p;
     p.R = R;
     p.nstages = (d.ntiles + R - 1) / R;
     const int64_t stage_bytes = j > 0 ? int64_t(R) * tb : int64_t(R) * kTile * ssize;
-    int cs = int(CHUNK_BYTES / (stage_bytes > 0 ? stage_bytes : 1));
+    int cs = int(a.chunk_bytes / (stage_bytes > 0 ? stage_bytes : 1));
     if (cs < 1) cs = 1;
     p.cs = cs;
     p.nchunks = (p.nstages + cs - 1) / cs;
@@ -136,17 +141,9 @@ __global__ void plan_kernel(BatchArgs a, int ssize) {
 }
 
 // ---------------------------------------------------------------------------- helpers
-__device__ __forceinline__ double block_sum_d(double v, double *red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < THREADS / 32; ++i) t += red[i];
-  __syncthreads();
-  return t;
-}
+struct Item {
+  int32_t valid, stream, phase, chunk;
+};
 
 // spin (bounded) until stream s has finished phase p-1
 __device__ bool wait_phase(const BatchArgs &a, int s, int p) {
@@ -160,82 +157,159 @@ __device__ bool wait_phase(const BatchArgs &a, int s, int p) {
   return true;
 }
 
+// Decode an item index into (phase, stream, chunk) by binary search over the item offsets.
+__device__ void decode_item(const BatchArgs &a, int item, int &phase, int &stream, int &chunk) {
+  const int S = a.S;
+  int lo = 0, hi = 5 * S;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (a.offs[mid] <= item) lo = mid;
+    else hi = mid;
+  }
+  while (lo + 1 <= 5 * S && a.offs[lo + 1] <= item) ++lo;  // skip empty entries
+  phase = lo / S;
+  stream = lo % S;
+  chunk = item - a.offs[lo];
+}
+
 template <typename S>
-__global__ void __launch_bounds__(THREADS, 1) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char *slotmem = smem;                                          // SLOTS x (SLOT_V + SLOT_B)
-  float *ws = reinterpret_cast<float *>(smem + SLOTS * (SLOT_V + SLOT_B));  // MAX_R*32
-  float *cf = ws + MAX_R * kTile;                                         // kMaxK
-  double *dot = reinterpret_cast<double *>(cf + kMaxK);                   // kMaxK + 1
-  double *comb = dot + kMaxK + 2;                                         // 256
-  double *red = comb + THREADS;                                           // 32
-  __shared__ uint64_t full[SLOTS];
-  __shared__ int s_item, s_stream, s_phase, s_chunk, s_last, s_fail;
+  const int slot_bytes = a.slot_v + SLOT_B;
+  unsigned char *slotmem = smem;                                                    // nslots x slot
+  float *wsb = reinterpret_cast<float *>(smem + size_t(a.nslots) * slot_bytes);    // 2 x MAX_R*32
+  float *cf = wsb + 2 * MAX_R * kTile;                                              // kMaxK + 8
+  double *dot = reinterpret_cast<double *>(cf + kMaxK + 8);                         // kMaxK + 2
+  float *combb = reinterpret_cast<float *>(dot + kMaxK + 2);                        // 2 x 256
+  double *nrm = reinterpret_cast<double *>(combb + 512);                            // 256
+  __shared__ uint64_t full[MAX_SLOTS], empty[MAX_SLOTS], ws_full[2], ws_empty[2], item_full[2], item_empty[2];
+  __shared__ Item ring[2];
+  __shared__ int s_abort, s_last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < SLOTS; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < a.nslots; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kWarps);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ws_full[b], ROW_WARPS);
+      mbar_init(&ws_empty[b], COL_WARPS);
+      mbar_init(&item_full[b], 1);
+      mbar_init(&item_empty[b], 1);
+    }
+    s_abort = 0;
     mbar_fence_init();
   }
   __syncthreads();
-  const int S_ = a.S;
   const int total = *a.total;
-  uint32_t it = 0;  // stages consumed by this CTA (mbarrier phase tracking)
-  while (true) {
-    __syncthreads();  // everyone is done with the previous item's descriptors
-    if (tid == 0) {
+  auto fail = [&]() {
+    s_abort = 1;
+    atomicExch(a.err, FOA_DMD_ETIMEOUT);
+  };
+
+  if (warp == kWarps) {
+    // ---------------------------------------------------------------- producer warp
+    if (lane != 0) return;
+    uint32_t it = 0;  // stages issued
+    for (int k = 0;; ++k) {
+      const int r = k & 1;
+      if (k >= 2 && !mbar_wait(&item_empty[r], ((k >> 1) - 1) & 1)) {
+        fail();
+        return;
+      }
       const int item = int(atomicAdd(a.counter, 1u));
-      s_item = item;
-      s_fail = 0;
-      if (item < total) {
-        // phase and stream by binary search over the item offsets
-        int lo = 0, hi = 5 * S_;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (a.offs[mid] <= item) lo = mid;
-          else hi = mid;
+      Item d;
+      d.valid = item < total && !s_abort;
+      if (d.valid) {
+        decode_item(a, item, d.phase, d.stream, d.chunk);
+        if (!wait_phase(a, d.stream, d.phase)) {
+          fail();
+          d.valid = 0;
         }
-        while (lo + 1 <= 5 * S_ && a.offs[lo + 1] <= item) ++lo;  // skip empty entries
-        s_phase = lo / S_;
-        s_stream = lo % S_;
-        s_chunk = item - a.offs[lo];
-        if (!wait_phase(a, s_stream, s_phase)) {
-          s_fail = 1;
-          atomicExch(a.err, FOA_DMD_ETIMEOUT);
+        __threadfence();  // the finished phase's results are visible to the consumers
+      }
+      ring[r] = d;
+      mbar_arrive(&item_full[r]);  // release: the descriptor
+      if (!d.valid) return;
+      if (d.phase < 1 || d.phase > 3) continue;  // beta_pre and append move no staged data
+      const StreamDesc sd = a.sd[d.stream];
+      const Plan pl = a.plan[d.stream];
+      const BState *bs = a.st + d.stream;
+      const bool first = __ldcg(&bs->first) != 0;
+      const int j = first ? 0 : __ldcg(&bs->j);
+      const int mode = first ? PASS_FIRST : (d.phase == 1 ? PASS_A : d.phase == 2 ? PASS_B : PASS_C);
+      const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
+      const S *Vs = static_cast<const S *>(a.V) + sd.v_off;
+      const S *x = static_cast<const S *>(a.x[d.stream]);
+      const float *w = a.W + sd.w_off;
+      const bool x_aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+      const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
+      const int s0 = d.chunk * pl.cs, s1 = min(pl.nstages, s0 + pl.cs);
+      for (int stg = s0; stg < s1; ++stg, ++it) {
+        const int slot = int(it % a.nslots);
+        if (it >= uint32_t(a.nslots) && !mbar_wait(&empty[slot], ((it / a.nslots) - 1) & 1)) {
+          fail();
+          return;
         }
-        __threadfence();  // acquire: the finished phase's results are visible below
+        const int t0 = stg * pl.R;
+        const int nt = min(pl.R, sd.ntiles - t0);
+        const int64_t r0 = int64_t(t0) * kTile;
+        unsigned char *dst = slotmem + size_t(slot) * slot_bytes;
+        const bool bb = base_x ? (x_aligned && r0 + int64_t(nt) * kTile <= sd.n) : true;
+        const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? sizeof(S) : 4) : 0u;
+        mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
+        if (tile_bytes)
+          for (int q = 0; q < nt; ++q)
+            bulk_g2s(dst + size_t(q) * tile_bytes, Vs + int64_t(t0 + q) * sd.kmax * kTile, tile_bytes, &full[slot]);
+        if (bbytes) {
+          if (base_x) bulk_g2s(dst + a.slot_v, x + r0, bbytes, &full[slot]);
+          else bulk_g2s(dst + a.slot_v, w + r0, bbytes, &full[slot]);
+        }
       }
     }
-    __syncthreads();
-    if (s_item >= total || s_fail) break;
-    const int sidx = s_stream, ph = s_phase, chunk = s_chunk;
-    const StreamDesc d = a.sd[sidx];
+  }
+
+  // ------------------------------------------------------------------ consumer warps
+  const bool rowg = warp < ROW_WARPS;
+  uint32_t it = 0;  // stages consumed (same sequence as the producer's)
+  float acc[NCB / 2];
+  for (int k = 0;; ++k) {
+    const int r = k & 1;
+    if (!s_abort && !mbar_wait(&item_full[r], (k >> 1) & 1)) fail();
+    const Item d = ring[r];
+    named_bar_sync(1, kConsumers);  // every consumer has read the descriptor
+    if (tid == 0) mbar_arrive(&item_empty[r]);
+    if (!d.valid || s_abort) break;
+    const int sidx = d.stream, ph = d.phase, chunk = d.chunk;
+    const StreamDesc sd = a.sd[sidx];
     BState *bs = a.st + sidx;
     const Plan pl = a.plan[sidx];
     const int j = __ldcg(&bs->j);
     const bool first = __ldcg(&bs->first) != 0;
-    const int K = d.kmax;
-    double *Hs = a.H + d.mat_off, *Bs = a.B + d.mat_off;
-    double *pre = a.vec + d.vec_off, *hv = pre + K, *sv = hv + K;
-    S *Vs = static_cast<S *>(a.V) + d.v_off;
-    float *w = a.W + d.w_off;
+    const int K = sd.kmax;
+    double *Hs = a.H + sd.mat_off, *Bs = a.B + sd.mat_off;
+    double *pre = a.vec + sd.vec_off, *hv = pre + K, *sv = hv + K;
+    S *Vs = static_cast<S *>(a.V) + sd.v_off;
+    float *w = a.W + sd.w_off;
     const S *x = static_cast<const S *>(a.x[sidx]);
-    const int64_t nrows = int64_t(d.ntiles) * kTile;
+    const int64_t nrows = int64_t(sd.ntiles) * kTile;
 
     if (ph == 0) {
       // ---------------------------------------------------------------- beta_pre (steps 5-8)
       if (tid == 0) {
-        bs->bjj = Bs[int64_t(j - 1) * (K + 1)];
-        bs->inv_bjj = 1.0 / bs->bjj;
+        const double bjj = __ldcg(Bs + int64_t(j - 1) * (K + 1));
+        bs->bjj = bjj;
+        bs->inv_bjj = 1.0 / bjj;
       }
-      for (int i = warp; i < j; i += THREADS / 32) {
+      for (int i = warp; i < j; i += kWarps) {
         const int l0 = i == 0 ? 0 : i - 1;
-        double acc = 0.0;
-        for (int l = l0 + lane; l <= j - 2; l += 32) acc += Hs[i + int64_t(l) * K] * Bs[l + int64_t(j - 1) * K];
-        acc = warp_sum(acc);
-        if (lane == 0) pre[i] = acc;
+        double s_ = 0.0;
+        for (int l = l0 + lane; l <= j - 2; l += 32) s_ += __ldcg(Hs + i + int64_t(l) * K) * __ldcg(Bs + l + int64_t(j - 1) * K);
+        s_ = warp_sum(s_);
+        if (lane == 0) pre[i] = s_;
       }
       __threadfence();
-      __syncthreads();
+      named_bar_sync(1, kConsumers);
       if (tid == 0) atomicExch(a.done + sidx, 0);
       continue;
     }
@@ -246,9 +320,9 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(BatchArgs a) {
       if (__ldcg(&bs->status) == FOA_DMD_OK) {
         const int64_t r0 = int64_t(s0) * pl.R * kTile, r1 = min(nrows, int64_t(s1) * pl.R * kTile);
         const float sc = float(__ldcg(&bs->inv_nu));
-        for (int64_t r = r0 + tid; r < r1; r += THREADS) {
-          const float v = first ? ((r < d.n) ? ldc(x, r) : 0.f) : w[r];
-          Vs[((r >> 5) * K + j) * kTile + (r & 31)] = Store<S>::from(v * sc);
+        for (int64_t rr = r0 + tid; rr < r1; rr += kConsumers) {
+          const float v = first ? ((rr < sd.n) ? float(to_c(x[rr])) : 0.f) : __ldcg(w + rr);
+          Vs[((rr >> 5) * K + j) * kTile + (rr & 31)] = Store<S>::from(v * sc);
         }
       }
       continue;
@@ -258,189 +332,191 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(BatchArgs a) {
     const bool dots = (mode == PASS_A || mode == PASS_B);
     const int jj = first ? 0 : j;
     const double *coef = (mode == PASS_A) ? pre : (mode == PASS_B) ? hv : sv;
-    const double cscale = (mode == PASS_A) ? __ldcg(&bs->inv_bjj) : 1.0;
-    for (int c = tid; c < jj; c += THREADS) cf[c] = float(__ldcg(coef + c));
-    for (int c = tid; c <= jj; c += THREADS) dot[c] = 0.0;
-    float acc[NC];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) acc[k] = 0.f;
-    double nacc = 0.0;
-    int since_flush = 0;
-    const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(jj) * sizeof(S);
-    const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
+    const float cscale = (mode == PASS_A) ? float(__ldcg(&bs->inv_bjj)) : 1.f;
+    for (int c = tid; c < ((jj + 7) & ~3); c += kConsumers) cf[c] = c < jj ? float(__ldcg(coef + c)) : 0.f;
+    for (int c = tid; c <= jj; c += kConsumers) dot[c] = 0.0;
     const bool x_aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    __syncthreads();
-    auto issue = [&](int stage, int slot) {
-      const int t0 = stage * pl.R;
-      const int nt = min(pl.R, d.ntiles - t0);
-      const int64_t r0 = int64_t(t0) * kTile;
-      unsigned char *dst = slotmem + size_t(slot) * (SLOT_V + SLOT_B);
-      const bool bb = base_x ? (x_aligned && r0 + int64_t(nt) * kTile <= d.n) : true;
-      const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? sizeof(S) : 4) : 0u;
-      mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
-      if (tile_bytes)
-        for (int k = 0; k < nt; ++k)
-          bulk_g2s(dst + size_t(k) * tile_bytes, Vs + (int64_t(t0 + k) * K) * kTile, tile_bytes, &full[slot]);
-      if (bbytes) {
-        if (base_x) bulk_g2s(dst + SLOT_V, x + r0, bbytes, &full[slot]);
-        else bulk_g2s(dst + SLOT_V, w + r0, bbytes, &full[slot]);
-      }
-    };
-    if (tid == 0) {
-      for (int k = 0; k < SLOTS && s0 + k < s1; ++k) issue(s0 + k, int((it + k) % SLOTS));
-    }
-    for (int stg = s0; stg < s1; ++stg, ++it) {
-      const int slot = int(it % SLOTS);
-      const int bad = mbar_wait(&full[slot], (it / SLOTS) & 1) ? 0 : 1;
-      if (__syncthreads_or(bad)) {
-        if (tid == 0) atomicExch(a.err, FOA_DMD_ETIMEOUT);
-        return;  // the handle is unusable after a timeout
-      }
-      const int t0 = stg * pl.R;
-      const int nt = min(pl.R, d.ntiles - t0);
-      const int RS = nt * kTile;
-      const int64_t r0 = int64_t(t0) * kTile;
-      const unsigned char *sb = slotmem + size_t(slot) * (SLOT_V + SLOT_B);
-      const S *vs = reinterpret_cast<const S *>(sb);
-      const bool bb = base_x ? (x_aligned && r0 + int64_t(RS) <= d.n) : true;
-      // sweep 1
-      const int G = (RS >= THREADS || jj == 0) ? 1 : (THREADS / RS);
-      float nst = 0.f;
-      if (tid < (G == 1 ? THREADS : G * RS)) {
-        const int g = (G == 1) ? 0 : tid / RS;
-        const int cpg = (jj + G - 1) / G;
-        const int c0 = g * cpg, c1 = min(jj, c0 + cpg);
-        for (int row = (G == 1 ? tid : tid % RS); row < RS; row += (G == 1 ? THREADS : RS)) {
-          const S *vr = vs + (row >> 5) * (kTile * jj) + (row & 31);
-          double accd = 0.0;
-          for (int cb = c0; cb < c1; cb += 32) {
-            const int ce = min(c1, cb + 32);
-            float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
-            int c = cb;
-            for (; c + 4 <= ce; c += 4) {
-              b0 = fmaf(to_c(vr[(c + 0) * kTile]), cf[c + 0], b0);
-              b1 = fmaf(to_c(vr[(c + 1) * kTile]), cf[c + 1], b1);
-              b2 = fmaf(to_c(vr[(c + 2) * kTile]), cf[c + 2], b2);
-              b3 = fmaf(to_c(vr[(c + 3) * kTile]), cf[c + 3], b3);
-            }
-            for (; c < ce; ++c) b0 = fmaf(to_c(vr[c * kTile]), cf[c], b0);
-            accd += double((b0 + b1) + (b2 + b3));
+    const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
+    named_bar_sync(1, kConsumers);
+    if (rowg) {
+      // ------------------------------------------------------------ row group: sweep 1
+      const int rt = tid;
+      float nsum = 0.f, ncomp = 0.f;
+      auto nrm_add = [&](float v) {
+        const float y = v - ncomp;
+        const float t = nsum + y;
+        ncomp = (t - nsum) - y;
+        nsum = t;
+      };
+      for (int stg = s0; stg < s1; ++stg, ++it) {
+        const int slot = int(it % a.nslots);
+        const int b = int(it & 1);
+        if (!s_abort && !mbar_wait(&full[slot], (it / a.nslots) & 1)) fail();
+        if (it >= 2 && !s_abort && !mbar_wait(&ws_empty[b], ((it >> 1) - 1) & 1)) fail();
+        float *ws = wsb + b * (MAX_R * kTile);
+        float *cb = combb + b * 256;
+        const int t0 = stg * pl.R;
+        const int nt = min(pl.R, sd.ntiles - t0);
+        const int RS = nt * kTile;
+        const int64_t r0 = int64_t(t0) * kTile;
+        const unsigned char *sb = slotmem + size_t(slot) * slot_bytes;
+        const S *vs = reinterpret_cast<const S *>(sb);
+        const bool bb = base_x ? (x_aligned && r0 + int64_t(RS) <= sd.n) : true;
+        auto finish_row = [&](int row, float accv) {
+          const int64_t rr = r0 + row;
+          float base;
+          if (base_x) base = bb ? float(to_c(reinterpret_cast<const S *>(sb + a.slot_v)[row]))
+                                : ((rr < sd.n) ? float(to_c(x[rr])) : 0.f);
+          else base = reinterpret_cast<const float *>(sb + a.slot_v)[row];
+          if (mode == PASS_FIRST) {
+            nrm_add(base * base);
+            return;
           }
-          if (G > 1) {
-            comb[g * RS + row] = accd;
-          } else {
-            const int64_t r = r0 + row;
-            double base;
-            if (base_x) base = bb ? double(to_c(reinterpret_cast<const S *>(sb + SLOT_V)[row]))
-                                  : ((r < d.n) ? double(ldc(x, r)) : 0.0);
-            else base = double(reinterpret_cast<const float *>(sb + SLOT_V)[row]);
-            if (mode == PASS_FIRST) {
-              const float xv = float(base);
-              nst = fmaf(xv, xv, nst);
-            } else {
-              const double wn = (mode == PASS_A) ? (base - accd) * cscale : (base - accd);
-              const float wc = float(wn);
-              w[r] = wc;
-              ws[row] = wc;
-              if (mode == PASS_A) {
-                const float xv = float(base);
-                nst = fmaf(xv, xv, nst);
-              } else if (mode == PASS_C) {
-                nst = fmaf(wc, wc, nst);
+          const float wc = (mode == PASS_A) ? (base - accv) * cscale : (base - accv);
+          w[rr] = wc;
+          ws[row] = wc;
+          if (mode == PASS_A) nrm_add(base * base);
+          else if (mode == PASS_C) nrm_add(wc * wc);
+        };
+        if (jj == 0) {
+          for (int row = rt; row < RS; row += ROW_THREADS) finish_row(row, 0.f);
+        } else {
+          // row pairs, column groups of a multiple of 4, 16-byte coefficient broadcasts
+          const int P = RS >> 1;
+          const int G1 = (P >= ROW_THREADS) ? 1 : (ROW_THREADS / P);
+          if (rt < (G1 == 1 ? ROW_THREADS : G1 * P)) {
+            const int g = (G1 == 1) ? 0 : rt / P;
+            const int cpg = (((jj + G1 - 1) / G1) + 3) & ~3;
+            const int c0 = g * cpg, c1 = min(jj, c0 + cpg);
+            for (int pr = (G1 == 1 ? rt : rt % P); pr < P; pr += (G1 == 1 ? ROW_THREADS : P)) {
+              const int row = 2 * pr;
+              const S *vr = vs + (row >> 5) * (kTile * jj) + (row & 31);
+              float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+              for (int c = c0; c < c1; c += 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(cf + c);
+                float2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = (c + u < c1) ? ld_pair(vr + (c + u) * kTile) : make_float2(0.f, 0.f);
+                a0[0] = fmaf(v[0].x, q.x, a0[0]); a1[0] = fmaf(v[0].y, q.x, a1[0]);
+                a0[1] = fmaf(v[1].x, q.y, a0[1]); a1[1] = fmaf(v[1].y, q.y, a1[1]);
+                a0[2] = fmaf(v[2].x, q.z, a0[2]); a1[2] = fmaf(v[2].y, q.z, a1[2]);
+                a0[3] = fmaf(v[3].x, q.w, a0[3]); a1[3] = fmaf(v[3].y, q.w, a1[3]);
+              }
+              const float sa = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+              const float sb_ = (a1[0] + a1[1]) + (a1[2] + a1[3]);
+              if (G1 > 1) {
+                cb[g * RS + row] = sa;
+                cb[g * RS + row + 1] = sb_;
+              } else {
+                finish_row(row, sa);
+                finish_row(row + 1, sb_);
               }
             }
           }
-        }
-      }
-      if (G > 1) {
-        __syncthreads();
-        if (tid < RS) {
-          double accd = 0.0;
-          for (int g = 0; g < G; ++g) accd += comb[g * RS + tid];
-          const int64_t r = r0 + tid;
-          double base;
-          if (base_x) base = bb ? double(to_c(reinterpret_cast<const S *>(sb + SLOT_V)[tid]))
-                                : ((r < d.n) ? double(ldc(x, r)) : 0.0);
-          else base = double(reinterpret_cast<const float *>(sb + SLOT_V)[tid]);
-          const double wn = (mode == PASS_A) ? (base - accd) * cscale : (base - accd);
-          const float wc = float(wn);
-          w[r] = wc;
-          ws[tid] = wc;
-          if (mode == PASS_A) {
-            const float xv = float(base);
-            nst = fmaf(xv, xv, nst);
-          } else if (mode == PASS_C) {
-            nst = fmaf(wc, wc, nst);
-          }
-        }
-      }
-      nacc += double(nst);
-      __syncthreads();
-      // sweep 2
-      if (dots) {
-        for (int kt = 0; kt < nt; ++kt) {
-          const float wv = ws[kt * kTile + lane];
-          const S *vt = vs + kt * (kTile * jj) + lane;
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const int c = warp + (THREADS / 32) * k;
-            if (c < jj) acc[k] = fmaf(to_c(vt[c * kTile]), wv, acc[k]);
-          }
-        }
-        since_flush += nt;
-        if (since_flush >= 32) {
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const int c = warp + (THREADS / 32) * k;
-            if (c < jj) {
-              const float v = warp_sum(acc[k]);
-              if (lane == 0) dot[c] += double(v);
-              acc[k] = 0.f;
+          if (G1 > 1) {
+            named_bar_sync(2, ROW_THREADS);
+            if (rt < RS) {
+              float s_ = 0.f;
+              for (int g = 0; g < G1; ++g) s_ += cb[g * RS + rt];
+              finish_row(rt, s_);
             }
           }
-          since_flush = 0;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&ws_full[b]);
+          mbar_arrive(&empty[slot]);
         }
       }
-      __syncthreads();
-      if (tid == 0 && stg + SLOTS < s1) issue(stg + SLOTS, slot);
-    }
-    // flush and write this chunk's partial
-    if (dots) {
+      nrm[tid] = double(nsum) - double(ncomp);
+    } else {
+      // --------------------------------------------------------- column group: sweep 2
+      const int cw = warp - ROW_WARPS;
+      const int hl = lane & 15, half = lane >> 4;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const int c = warp + (THREADS / 32) * k;
-        if (c < jj) {
-          const float v = warp_sum(acc[k]);
-          if (lane == 0) dot[c] += double(v);
+      for (int q = 0; q < NCB / 2; ++q) acc[q] = 0.f;
+      auto flush = [&]() {
+#pragma unroll
+        for (int kk = 0; kk < NCB / 2; ++kk) {
+          const int c = cw + COL_WARPS * (2 * kk + half);
+          if (cw + COL_WARPS * (2 * kk) < jj) {  // warp-uniform
+            float v = (c < jj) ? acc[kk] : 0.f;
+#pragma unroll
+            for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (hl == 0 && c < jj) dot[c] += double(v);
+            acc[kk] = 0.f;
+          }
+        }
+      };
+      int since_flush = 0;
+      for (int stg = s0; stg < s1; ++stg, ++it) {
+        const int slot = int(it % a.nslots);
+        const int b = int(it & 1);
+        if (!s_abort && !mbar_wait(&full[slot], (it / a.nslots) & 1)) fail();
+        if (!s_abort && !mbar_wait(&ws_full[b], (it >> 1) & 1)) fail();
+        if (dots) {
+          const float *ws = wsb + b * (MAX_R * kTile);
+          const int t0 = stg * pl.R;
+          const int nt = min(pl.R, sd.ntiles - t0);
+          const S *vs = reinterpret_cast<const S *>(slotmem + size_t(slot) * slot_bytes);
+          for (int kt = 0; kt < nt; ++kt) {
+            const float2 wv = *reinterpret_cast<const float2 *>(ws + kt * kTile + 2 * hl);
+            const S *vt = vs + kt * (kTile * jj) + 2 * hl;
+#pragma unroll
+            for (int kk = 0; kk < NCB / 2; ++kk) {
+              const int c = cw + COL_WARPS * (2 * kk + half);
+              if (c < jj) {
+                const float2 v = ld_pair(vt + c * kTile);
+                acc[kk] = fmaf(v.x, wv.x, fmaf(v.y, wv.y, acc[kk]));
+              }
+            }
+          }
+          since_flush += nt;
+          if (since_flush >= 16) {
+            flush();
+            since_flush = 0;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&ws_empty[b]);
+          mbar_arrive(&empty[slot]);
         }
       }
+      if (dots) flush();
+      nrm[tid] = 0.0;
     }
-    const double ntot = block_sum_d(nacc, red);
-    if (tid == 0) dot[jj] = ntot;
-    __syncthreads();
-    double *pp = a.part + d.part_off + int64_t(chunk) * (K + 1);
-    for (int c = tid; c <= jj; c += THREADS) pp[c] = dot[c];
+    // ---------------------------------------------------------------- this chunk's partial
+    named_bar_sync(1, kConsumers);
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kConsumers; ++i) t += nrm[i];
+      dot[jj] = t;
+    }
+    named_bar_sync(1, kConsumers);
+    double *pp = a.part + sd.part_off + int64_t(chunk) * (K + 1);
+    for (int c = tid; c <= jj; c += kConsumers) pp[c] = dot[c];
     __threadfence();
-    __syncthreads();
+    named_bar_sync(1, kConsumers);
     if (tid == 0) {
       const unsigned t = atomicAdd(a.tickets + sidx * 5 + ph, 1u);
       s_last = (t == unsigned(pl.nchunks - 1)) ? 1 : 0;
     }
-    __syncthreads();
+    named_bar_sync(1, kConsumers);
     if (!s_last) continue;
     __threadfence();
     // ------------------------------------------------------------------ last chunk: reduce + scalar part
-    for (int c = tid; c <= jj; c += THREADS) {
+    for (int c = tid; c <= jj; c += kConsumers) {
       double t = 0.0;
-      for (int b = 0; b < pl.nchunks; ++b) t += __ldcg(a.part + d.part_off + int64_t(b) * (K + 1) + c);
+      for (int q = 0; q < pl.nchunks; ++q) t += __ldcg(a.part + sd.part_off + int64_t(q) * (K + 1) + c);
       dot[c] = t;
     }
-    __syncthreads();
+    named_bar_sync(1, kConsumers);
     if (mode == PASS_A) {
-      for (int c = tid; c < jj; c += THREADS) hv[c] = dot[c];
+      for (int c = tid; c < jj; c += kConsumers) hv[c] = dot[c];
       if (tid == 0) bs->x_norm = sqrt(dot[jj]);
     } else if (mode == PASS_B) {
-      for (int c = tid; c < jj; c += THREADS) {
+      for (int c = tid; c < jj; c += kConsumers) {
         sv[c] = dot[c];
         hv[c] = __ldcg(hv + c) + dot[c];
       }
@@ -452,10 +528,10 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(BatchArgs a) {
       else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
       else status = FOA_DMD_OK;
       if (status != FOA_DMD_ENONFINITE)
-        for (int c = tid; c < jj; c += THREADS) Hs[c + int64_t(jj - 1) * K] = __ldcg(hv + c);
+        for (int c = tid; c < jj; c += kConsumers) Hs[c + int64_t(jj - 1) * K] = __ldcg(hv + c);
       if (status == FOA_DMD_OK)
-        for (int c = tid; c < jj; c += THREADS) Bs[c + int64_t(jj) * K] = __ldcg(pre + c) + __ldcg(hv + c) * bjj;
-      __syncthreads();
+        for (int c = tid; c < jj; c += kConsumers) Bs[c + int64_t(jj) * K] = __ldcg(pre + c) + __ldcg(hv + c) * bjj;
+      named_bar_sync(1, kConsumers);
       if (tid == 0) {
         if (status == FOA_DMD_OK) {
           Hs[jj + int64_t(jj - 1) * K] = nu;
@@ -473,24 +549,24 @@ __global__ void __launch_bounds__(THREADS, 1) batch_kernel(BatchArgs a) {
       }
     } else {  // first snapshot
       if (tid == 0) {
-        const double b = sqrt(dot[0]);
-        int status = !isfinite(b) ? FOA_DMD_ENONFINITE : (!(b > 0.0) ? FOA_DMD_EBREAKDOWN : FOA_DMD_OK);
+        const double bn = sqrt(dot[0]);
+        int status = !isfinite(bn) ? FOA_DMD_ENONFINITE : (!(bn > 0.0) ? FOA_DMD_EBREAKDOWN : FOA_DMD_OK);
         if (status == FOA_DMD_OK) {
-          Bs[0] = b;
-          bs->inv_nu = 1.0 / b;
-          bs->nu = b;
+          Bs[0] = bn;
+          bs->inv_nu = 1.0 / bn;
+          bs->nu = bn;
           bs->q = 1;
-          if (a.h_last) a.h_last[sidx] = b;
+          if (a.h_last) a.h_last[sidx] = bn;
         } else if (status == FOA_DMD_EBREAKDOWN) {
           bs->stopped = 1;
         }
-        bs->x_norm = b;
-        bs->h_last = b;
+        bs->x_norm = bn;
+        bs->h_last = bn;
         bs->status = status;
       }
     }
     __threadfence();
-    __syncthreads();
+    named_bar_sync(1, kConsumers);
     // first snapshot: passes B and C do not exist, so completing the norm completes phase 3
     if (tid == 0) atomicExch(a.done + sidx, (mode == PASS_FIRST) ? 3 : ph);
   }
@@ -516,6 +592,8 @@ struct foa_dmd_batch {
   float *W = nullptr;
   double *H = nullptr, *B = nullptr, *vec = nullptr, *part = nullptr;
   size_t smem = 0;
+  int32_t slot_v = 0, nslots = 0;
+  int64_t chunk_bytes = 0;
 };
 
 static void batch_free(foa_dmd_batch *b) {
@@ -546,6 +624,18 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
   b->stream = static_cast<cudaStream_t>(o.cuda_stream);
   b->tol = o.breakdown_tol > 0.0 ? o.breakdown_tol : default_tol(dtype);
   const int es = dtype_size(dtype);
+  // a stage slot holds one whole 32-row tile of the widest stream; the ring is as deep as fits
+  int kmax_max = 2;
+  for (int s = 0; s < S; ++s) kmax_max = k_max[s] > kmax_max ? k_max[s] : kmax_max;
+  b->slot_v = int32_t((int64_t(kTile) * kmax_max * es + 127) / 128 * 128);
+  if (b->slot_v < 16384) b->slot_v = 16384;
+  const size_t fixed = size_t(2) * MAX_R * kTile * 4 + size_t(kMaxK + 8) * 4 + size_t(kMaxK + 2) * 8 + 512 * 4 +
+                       size_t(kConsumers) * 8;
+  int nslots = MAX_SLOTS;
+  while (nslots > 2 && size_t(nslots) * (b->slot_v + SLOT_B) + fixed > size_t(220) * 1024) --nslots;
+  b->nslots = nslots;
+  b->chunk_bytes = 16ll << 20;  // V bytes per work item
+  b->smem = size_t(nslots) * (b->slot_v + SLOT_B) + fixed;
   int64_t voff = 0, woff = 0, moff = 0, vecoff = 0, poff = 0;
   b->sd_host.resize(S);
   for (int s = 0; s < S; ++s) {
@@ -564,7 +654,7 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
     moff += int64_t(d.kmax) * d.kmax;
     d.vec_off = vecoff;
     vecoff += 3 * int64_t(d.kmax);
-    d.max_chunks = int32_t(int64_t(nrows) * d.kmax * es / CHUNK_BYTES + 2);
+    d.max_chunks = int32_t(int64_t(nrows) * d.kmax * es / b->chunk_bytes + 2);
     d.part_off = poff;
     poff += int64_t(d.max_chunks) * (d.kmax + 1);
     d.pad = 0;
@@ -597,8 +687,6 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
   if (e == cudaSuccess) e = cudaMemset(b->W, 0, size_t(woff) * 4);
   if (e == cudaSuccess) e = cudaMemset(b->H, 0, size_t(moff) * 8);
   if (e == cudaSuccess) e = cudaMemset(b->B, 0, size_t(moff) * 8);
-  b->smem = size_t(SLOTS) * (SLOT_V + SLOT_B) + size_t(MAX_R) * kTile * 4 + size_t(kMaxK) * 4 +
-            size_t(kMaxK + 2) * 8 + size_t(THREADS) * 8 + 32 * 8;
   if (e == cudaSuccess) {
     e = cudaFuncSetAttribute(dtype == FOA_DMD_F32 ? (const void *)batch_kernel<float>
                                                    : (const void *)batch_kernel<__nv_bfloat16>,
@@ -636,13 +724,16 @@ extern "C" int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, 
   a.tol = b->tol;
   a.S = b->S;
   a.err = b->err;
+  a.slot_v = b->slot_v;
+  a.nslots = b->nslots;
+  a.chunk_bytes = b->chunk_bytes;
   plan_kernel<<<1, 256, size_t(5) * b->S * 4, b->stream>>>(a, dtype_size(b->dtype));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   // one CTA per SM, all co-resident (cooperative launch), so the in-kernel phase waits always end
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->sms);
-  cfg.blockDim = dim3(THREADS);
+  cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = b->smem;
   cfg.stream = b->stream;
   cudaLaunchAttribute attr[1];
