@@ -64,6 +64,8 @@ def load(path):
     L.foa_oracle_step.restype = ctypes.c_int
     L.foa_oracle_qr_step.argtypes = [i64, i32, P, i64, P, i32, P, i32, P, d, ctypes.c_int, P]
     L.foa_oracle_qr_step.restype = ctypes.c_int
+    L.foa_oracle_block_step.argtypes = [i64, i32, i32, P, i64, P, i32, P, i32, P, i64, d, P]
+    L.foa_oracle_block_step.restype = ctypes.c_int
     return L
 
 
@@ -144,6 +146,47 @@ class FoaOracle:
         self.q += 1
         self.h_last.append(float(out[0]))
         return "ok", float(out[0]), float(out[1])
+
+    def push_block(self, X):
+        """Block push of the columns of X (n x p) at once: block CGS2 against V and Cholesky QR twice
+        (the block form of the QR view); returns one status tuple per snapshot as push() does.  A
+        stream with no basis yet starts with a single push of the first column."""
+        X = np.asfortranarray(X, dtype=np.float64)
+        n, p = X.shape
+        assert n == self.n
+        res = []
+        t = 0
+        if self.q == 0 and p > 0:
+            res.append(self.push(X[:, 0]))
+            t = 1
+            if res[-1][0] != "ok":
+                return res + [("stopped", float("nan"), float("nan"))] * (p - 1)
+        if self.stopped:
+            return res + [("stopped", float("nan"), float("nan"))] * (p - t)
+        pb = min(p - t, self.k_max - self.q)
+        if pb > 0:
+            Xb = np.asfortranarray(X[:, t:t + pb])
+            if not np.all(np.isfinite(Xb)):
+                return res + [("nonfinite", float("nan"), float("nan"))] * (p - t)
+            out = np.zeros(1 + pb)
+            L = self._L or lib()
+            st = L.foa_oracle_block_step(self.n, self.q, pb, _ptr(self.V), self.n, _ptr(self.H), self.k_max,
+                                         _ptr(self.B), self.k_max, _ptr(Xb), self.n, self.tol, _ptr(out))
+            if st == NOMEM:
+                raise MemoryError
+            nc = int(out[0])
+            for i in range(nc):
+                res.append(("ok", float(out[1 + i]), float(np.linalg.norm(Xb[:, i]))))
+                self.h_last.append(float(out[1 + i]))
+            self.q += nc
+            if st == BREAKDOWN:
+                self.stopped = True
+                res.append(("breakdown", 0.0, float(np.linalg.norm(Xb[:, nc]))))
+                res += [("stopped", float("nan"), float("nan"))] * (p - t - nc - 1)
+                return res
+            t += pb
+        res += [("full", float("nan"), float("nan"))] * (p - t)
+        return res
 
     def push_batch(self, X):
         """Algorithm 4 with p = X.shape[1]: the same per-snapshot steps in sequence."""

@@ -261,4 +261,164 @@ int foa_oracle_qr_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, 
   return status;
 }
 
+/*
+ * Block push of p snapshots at once (the block form of the QR view: block classical Gram-Schmidt
+ * with reorthogonalisation against V, then a Cholesky QR of the projected block, twice).  In exact
+ * arithmetic it gives the same V, beta and Hbar as p single pushes (the QR factorisation of X with
+ * a positive diagonal is unique, Sec. 3.1); the rounding differs.  Steps, X_b = [psi_{j+1} ..
+ * psi_{j+p}] (n x p, leading dimension ldx):
+ *   C1 = V^T X_b;  W = X_b - V C1;  C2 = V^T W;  W = W - V C2;  C = C1 + C2
+ *   G = W^T W = R1^T R1 (Cholesky);  W1 = W R1^-1;  G2 = W1^T W1 = R2^T R2;  Q = W1 R2^-1;  R = R2 R1
+ *   beta_{1:j, j+1:j+p} = C,  beta_{j+1:j+p, j+1:j+p} = R,  V_{:, j+1:j+p} = Q
+ * and the Hbar columns j .. j+p-1 by the forward substitution of foa_oracle_qr_step, one column
+ * after the other.  Breakdown: the first block column i with R_ii <= tol * ||psi_{j+1+i}||_2 (or a
+ * Cholesky pivot <= 0) is dependent; the columns before it are committed, its Hbar column gets a
+ * zero subdiagonal, and ORACLE_BREAKDOWN returns with out[0] = i (columns committed).
+ * out[1 + i] = Hbar_{j+1+i, j+i} for the committed columns.
+ */
+static int chol_upper(int p, const double *G, int ldg, double *R, int ldr) {
+  /* G = R^T R for the leading block that stays positive definite, R upper triangular (column-
+     major); returns the number of leading columns factored (the first failing pivot, or p) */
+  for (int c = 0; c < p; ++c)
+    for (int r = 0; r < p; ++r) R[r + c * ldr] = 0.0;
+  for (int i = 0; i < p; ++i) {
+    double d = G[i + i * ldg];
+    for (int k = 0; k < i; ++k) d -= R[k + i * ldr] * R[k + i * ldr];
+    if (!(d > 0.0)) return i;
+    double rii = sqrt(d);
+    R[i + i * ldr] = rii;
+    for (int c = i + 1; c < p; ++c) {
+      double t = G[i + c * ldg];
+      for (int k = 0; k < i; ++k) t -= R[k + i * ldr] * R[k + c * ldr];
+      R[i + c * ldr] = t / rii;
+    }
+  }
+  return p;
+}
+
+/* W[:, :m] (n rows, column stride n) := W[:, :m] R^-1, R upper triangular (leading dimension ldr) */
+static void right_solve_upper(int64_t n, int m, double *W, const double *R, int ldr) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < n; ++r) {
+    for (int c = 0; c < m; ++c) {
+      double t = W[r + (int64_t)c * n];
+      for (int k = 0; k < c; ++k) t -= W[r + (int64_t)k * n] * R[k + c * ldr];
+      W[r + (int64_t)c * n] = t / R[c + c * ldr];
+    }
+  }
+}
+
+/* G = W[:, :m]^T W[:, :m] (leading dimension ldg), each entry a blocked dot product */
+static void gram_blocked(int64_t n, int m, const double *W, double *G, int ldg, double *part) {
+  for (int a = 0; a < m; ++a)
+    for (int b = a; b < m; ++b) {
+      double g = dot_blocked(n, W + (int64_t)a * n, W + (int64_t)b * n, part);
+      G[a + b * ldg] = g;
+      G[b + a * ldg] = g;
+    }
+}
+
+int foa_oracle_block_step(int64_t n, int32_t j, int32_t p, double *V, int64_t ldv, double *H, int32_t ldh,
+                          double *B, int32_t ldb, const double *X, int64_t ldx, double tol, double *out) {
+  out[0] = 0.0;
+  if (p < 1) return ORACLE_OK;
+  int64_t nb = nblocks_of(n);
+  double *W = (double *)malloc(sizeof(double) * (size_t)(n * p));
+  double *Y = (double *)malloc(sizeof(double) * (size_t)n);
+  double *part = (double *)malloc(sizeof(double) * (size_t)(nb * (j > 1 ? j : 1)));
+  double *C = (double *)calloc((size_t)(j * p), sizeof(double));
+  double *C2 = (double *)calloc((size_t)j, sizeof(double));
+  double *G = (double *)calloc((size_t)(p * p), sizeof(double));
+  double *R1 = (double *)calloc((size_t)(p * p), sizeof(double));
+  double *R2 = (double *)calloc((size_t)(p * p), sizeof(double));
+  double *R = (double *)calloc((size_t)(p * p), sizeof(double));
+  double *xn = (double *)malloc(sizeof(double) * (size_t)p);
+  if (!W || !Y || !part || !C || !C2 || !G || !R1 || !R2 || !R || !xn) {
+    free(W); free(Y); free(part); free(C); free(C2); free(G); free(R1); free(R2); free(R); free(xn);
+    return ORACLE_NOMEM;
+  }
+#define HB(i, l) H[(int64_t)(l) * ldh + (i)]
+#define BT(i, l) B[(int64_t)(l) * ldb + (i)]
+  /* block Gram-Schmidt against V, twice */
+  for (int k = 0; k < p; ++k) {
+    const double *x = X + (int64_t)k * ldx;
+    double *w = W + (int64_t)k * n;
+    double *ck = C + (int64_t)k * j;
+    xn[k] = sqrt(dot_blocked(n, x, x, part));
+    gemv_t(n, j, V, ldv, x, ck, part);                          /* C1 = V^T X_b */
+    gemv_n(n, j, V, ldv, ck, Y);
+    for (int64_t r = 0; r < n; ++r) w[r] = x[r] - Y[r];          /* W = X_b - V C1 */
+    gemv_t(n, j, V, ldv, w, C2, part);                          /* C2 = V^T W */
+    gemv_n(n, j, V, ldv, C2, Y);
+    for (int64_t r = 0; r < n; ++r) w[r] = w[r] - Y[r];          /* W = W - V C2 */
+    for (int i = 0; i < j; ++i) ck[i] = ck[i] + C2[i];          /* C = C1 + C2 */
+  }
+  /* Cholesky QR twice on the leading columns that stay positive definite */
+  gram_blocked(n, p, W, G, p, part);                           /* G = W^T W */
+  const int m1 = chol_upper(p, G, p, R1, p);                   /* G = R1^T R1, leading m1 columns */
+  int m = m1;
+  if (m1 > 0) {
+    right_solve_upper(n, m1, W, R1, p);                        /* W1 = W R1^-1 */
+    gram_blocked(n, m1, W, G, p, part);                        /* G2 = W1^T W1 */
+    m = chol_upper(m1, G, p, R2, p);                           /* G2 = R2^T R2, leading m columns */
+    if (m > 0) right_solve_upper(n, m, W, R2, p);              /* Q = W1 R2^-1 */
+  }
+  /* R = R2 R1: rows r < m are defined for every column c (R1's rows below m1 are not: a column
+     past the factored block keeps its coefficients on the factored directions) */
+  for (int c = 0; c < p; ++c)
+    for (int r = 0; r < m && r <= c; ++r) {
+      double t = 0.0;
+      const int kmax = c < m1 - 1 ? c : m1 - 1;
+      for (int k = r; k <= kmax; ++k) t += R2[r + k * p] * R1[k + c * p];
+      R[r + c * p] = t;
+    }
+  /* the first dependent column: R_ii <= tol ||psi|| (or no factor) */
+  int ncommit = 0;
+  int status = ORACLE_OK;
+  for (int i = 0; i < p; ++i) {
+    if (!(i < m && R[i + i * p] > tol * xn[i])) {
+      status = ORACLE_BREAKDOWN;
+      break;
+    }
+    ncommit = i + 1;
+  }
+  /* commits: beta block column, V */
+  for (int i = 0; i < ncommit; ++i) {
+    const int col = j + i;
+    for (int r = 0; r < j; ++r) BT(r, col) = C[r + (int64_t)i * j];
+    for (int r = 0; r <= i; ++r) BT(j + r, col) = R[r + i * p];
+    double *vn = V + (int64_t)col * ldv;
+    const double *qc = W + (int64_t)i * n;
+    for (int64_t r = 0; r < n; ++r) vn[r] = qc[r];
+  }
+  /* Hbar columns by forward substitution (as foa_oracle_qr_step), one per new snapshot; the first
+     dependent snapshot's column is formed from its coefficients with a zero subdiagonal */
+  const int ncols = ncommit + (status == ORACLE_BREAKDOWN ? 1 : 0);
+  for (int i = 0; i < ncols; ++i) {
+    const int jc = j - 1 + i;          /* 0-based Hbar column of snapshot j+i (basis size j+i before it) */
+    const int jj = j + i;
+    const double bjj = BT(jc, jc);
+    for (int r = 0; r < jj; ++r) {
+      double brc;                      /* beta_{r, jj} of snapshot j+i */
+      if (r < j) brc = C[r + (int64_t)i * j];
+      else brc = R[(r - j) + i * p];   /* r - j < i <= m: a factored row */
+      int l0 = r == 0 ? 0 : r - 1;
+      double acc = 0.0;
+      for (int l = l0; l <= jc - 1; ++l) acc += HB(r, l) * BT(l, jc);
+      HB(r, jc) = (brc - acc) / bjj;
+    }
+    if (i < ncommit) {
+      HB(jj, jc) = R[i + i * p] / bjj;
+      out[1 + i] = HB(jj, jc);
+    } else {
+      HB(jj, jc) = 0.0;
+    }
+  }
+  out[0] = (double)ncommit;
+#undef HB
+#undef BT
+  free(W); free(Y); free(part); free(C); free(C2); free(G); free(R1); free(R2); free(R); free(xn);
+  return status;
+}
+
 int foa_oracle_block_rows(void) { return ORACLE_BLOCK; }

@@ -378,6 +378,67 @@ def test_qr_view_planted_breakdown():
     assert d.max() <= 1e-9
 
 
+def run_blocks(X, p, k_max=None, tol=None, library=None):
+    """Block pushes of p columns at a time (the first column alone)."""
+    n, N = X.shape
+    o = oracle.FoaOracle(n, k_max or N, breakdown_tol=tol, library=library, form="qr")
+    o.push(X[:, 0])
+    for s in range(1, N, p):
+        st = o.push_block(X[:, s:s + p])
+        if any(x[0] != "ok" for x in st):
+            break
+    return o
+
+
+def test_block_push_is_the_householder_qr():
+    """Block push (block CGS2 + Cholesky QR twice, Sec. 3.1's QR view in blocks): beta is LAPACK's R
+    of X and V its Q (signs fixed), beta_{:,2:} = Hbar beta (Eq. matmulhbeta) to rounding."""
+    X = np.random.default_rng(8).standard_normal((400, 21))
+    for p in (2, 4):
+        o = run_blocks(X, p)
+        assert o.q == 21
+        Q, R = np.linalg.qr(X)
+        sg = np.sign(np.diag(R))
+        Q, R = Q * sg[None, :], R * sg[:, None]
+        assert np.linalg.norm(o.B[:21, :21] - R) <= 100 * U64 * np.linalg.norm(R)
+        assert np.linalg.norm(o.V[:, :21] - Q) <= 100 * U64 * 21
+        m = o.m
+        assert np.linalg.norm(o.B[:m + 1, 1:m + 1] - o.H[:m + 1, :m] @ o.B[:m, :m]) <= 100 * U64 * np.linalg.norm(o.B)
+
+
+def test_block_push_equals_single_pushes():
+    """In exact arithmetic the block push is p single pushes: the states agree to O(eps kappa) on a
+    well-conditioned and an ill-conditioned (Vandermonde) sequence, and V stays orthonormal."""
+    for X in (np.random.default_rng(9).standard_normal((300, 17)), synth.vandermonde_sequence(9, seed=6)[1]):
+        a = run_oracle(X, tol=1e-300, form="qr")
+        b = run_blocks(X, 4, tol=1e-300)
+        assert a.q == b.q
+        q, m = a.q, a.m
+        s = np.linalg.svd(X[:, :q], compute_uv=False)
+        kap = s[0] / s[-1]
+        assert np.linalg.norm(a.B[:q, :q] - b.B[:q, :q]) <= 1e3 * U64 * kap * np.linalg.norm(a.B[:q, :q])
+        assert np.linalg.norm(a.H[:m + 1, :m] - b.H[:m + 1, :m]) <= 1e3 * U64 * kap * np.linalg.norm(a.H[:m + 1, :m])
+        assert np.linalg.norm(np.eye(q) - b.V[:, :q].T @ b.V[:, :q], 2) <= 1e3 * U64 * max(1.0, kap * U64 * 1e8)
+
+
+def test_block_push_breakdown_inside_a_block():
+    """Planted rank-10 map pushed in blocks of 4: snapshot 11 (second column of the third block)
+    is dependent; the block commits its first column, stops, and the planted eigenvalues follow."""
+    spec = synth.config1(0)
+    X = synth.snapshots(spec)
+    o = oracle.FoaOracle(spec.n, 32, form="qr")
+    o.push(X[:, 0])
+    sts = []
+    for s in range(1, 32, 4):
+        sts += o.push_block(X[:, s:s + 4])
+        if o.stopped:
+            break
+    assert [x[0] for x in sts][:10] == ["ok"] * 9 + ["breakdown"]
+    assert o.stopped and o.q == 10 and o.m == 10 and o.H[10, 9] == 0.0
+    d, _ = match_eigs(o.eig(0.0)["lam"], spec.lam)
+    assert d.max() <= 1e-9
+
+
 # ------------------------------------------------------------------ planted mistakes
 MUTANTS = {
     "drop_second_projection": ("gemv_n(n, j, V, ldv, s, y);\n    for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];",
@@ -439,6 +500,66 @@ def _form_pins_pass(library, form):
         return True
     except Exception:
         return False
+
+
+BLOCK_MUTANTS = {
+    "block_no_second_projection": (
+        "gemv_n(n, j, V, ldv, C2, Y);\n    for (int64_t r = 0; r < n; ++r) w[r] = w[r] - Y[r];",
+        "gemv_n(n, j, V, ldv, C2, Y);\n    for (int64_t r = 0; r < n; ++r) w[r] = w[r];"),
+    "block_skip_first_cholesky_solve": ("    right_solve_upper(n, m1, W, R1, p);", "    (void)R1;"),
+    "block_hbar_subdiag_unscaled": ("      HB(jj, jc) = R[i + i * p] / bjj;", "      HB(jj, jc) = R[i + i * p];"),
+}
+
+
+def _block_pins_pass(library):
+    """The block push's pins: orthogonality, X = V beta and the Arnoldi Hbar (A known) on a random map,
+    orthogonality and X = V beta on the Vandermonde sequence."""
+    try:
+        rng = np.random.default_rng(3)
+        n, N = 60, 13
+        A = rng.standard_normal((n, n)) / np.sqrt(n)
+        X = np.empty((n, N))
+        X[:, 0] = rng.standard_normal(n)
+        for t in range(1, N):
+            X[:, t] = A @ X[:, t - 1]
+        o = run_blocks(X, 4, library=library)
+        if o.q != N:
+            return False
+        V, B = o.V[:, :N], o.B[:N, :N]
+        if np.linalg.norm(np.eye(N) - V.T @ V, 2) > 10 * N * U64:
+            return False
+        if np.linalg.norm(X - V @ B) > 10 * N * U64 * np.linalg.norm(X):
+            return False
+        Va, Ha = arnoldi(A, X[:, 0], N)
+        s = np.linalg.svd(X[:, :N - 1], compute_uv=False)
+        if np.linalg.norm(o.H[:N, :N - 1] - Ha) > 1e3 * U64 * s[0] / s[-1] * np.linalg.norm(Ha):
+            return False
+        A2, X2 = synth.vandermonde_sequence(9, seed=1)
+        o2 = run_blocks(X2, 4, tol=1e-300, library=library)
+        q2 = o2.q
+        V2, B2 = o2.V[:, :q2], o2.B[:q2, :q2]
+        if np.linalg.norm(np.eye(q2) - V2.T @ V2, 2) > 1e-6:  # Cholesky QR: O(u kappa(W)^2), measured 1e-9
+            return False
+        if np.linalg.norm(X2[:, :q2] - V2 @ B2) > 10 * 9 * U64 * np.linalg.norm(X2[:, :q2]):
+            return False
+        return True
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(BLOCK_MUTANTS))
+def test_block_mutants_are_caught(name, tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "foa_oracle.c")).read()
+    old, new = BLOCK_MUTANTS[name]
+    assert src.count(old) == 1
+    path = tmp_path / "mut.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(so),
+                    str(path), "-lm"], check=True)
+    assert _block_pins_pass(oracle.lib()), "block pins must hold on the real oracle"
+    assert not _block_pins_pass(oracle.load(str(so))), f"mutant {name} was not caught"
 
 
 @pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
