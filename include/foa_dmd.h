@@ -270,6 +270,27 @@ int foa_dmd_profile(foa_dmd_t *h, int enable);
 int foa_dmd_profile_read(foa_dmd_t *h, foa_dmd_kernel_stats *stats);
 
 /*
+ * Block push (no counterpart in Alg. 4, whose p snapshots are pushed one after the other): the
+ * snapshots are taken `block` at a time (2 or 4), each block orthogonalised against V by block
+ * classical Gram-Schmidt with one reorthogonalisation and then inside the block by Cholesky QR,
+ * twice; the beta block column is [C; R] and the H-bar columns follow from beta_{:,2:} = H-bar beta
+ * (App. B, Eq. matmulhbeta) by forward substitution, as in the QR view (foa_dmd_opts.form = 1).
+ * In exact arithmetic the result is that of p single pushes (X = V beta is the unique QR
+ * factorisation with a positive diagonal, Sec. 3.1); the rounding differs, and Cholesky QR loses
+ * orthogonality as O(u kappa(W)^2) when a block is nearly dependent on the basis.  V is read three
+ * times per block instead of three times per snapshot.
+ *   X_dev: device, p snapshots, snapshot t at X_dev + t*ld elements (storage dtype, 16-byte
+ *          aligned rows: ld * element size a multiple of 16); block: 2 or 4.
+ *   infos: host, p results (or NULL).  The first snapshot of a stream, a remainder shorter than
+ *          `block` and the columns just below k_max are pushed singly (with the handle's form).
+ * A dependent snapshot inside a block commits the columns before it and stops the stream
+ * (EBREAKDOWN; later snapshots ESTOPPED).  FP32/BF16 storage only (EINVAL for FP64).  The push-
+ * time indicator schedule is not run by block pushes.  Synchronises the handle's stream.
+ */
+int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld, int32_t block,
+                       foa_dmd_push_info *infos);
+
+/*
  * Autotuner of the streaming-pass launch geometry (no counterpart in the paper).  For every pass
  * kind the handle's options use (A/B/C, or the two passes of reorth = 2) and every j bucket up to
  * k_max (upper ends 8, 16, 32, 64, 128, 192, 256, 320, 384, 448, 512), times each candidate

@@ -213,30 +213,6 @@ int alloc_handle(foa_dmd *h) {
   return cuda_status(e);
 }
 
-// Record an event pair around a pass launch when profiling.
-struct ProfScope {
-  foa_dmd *h;
-  int kind;
-  double bytes;
-  size_t idx;
-  ProfScope(foa_dmd *h_, int kind_, double bytes_) : h(h_), kind(kind_), bytes(bytes_), idx(size_t(-1)) {
-    if (!h->prof) return;
-    if (h->prof_used == h->events.size()) {
-      EventPair p;
-      cudaEventCreate(&p.start);
-      cudaEventCreate(&p.stop);
-      h->events.push_back(p);
-    }
-    idx = h->prof_used++;
-    h->events[idx].kind = kind;
-    h->events[idx].bytes = bytes;
-    cudaEventRecord(h->events[idx].start, h->stream);
-  }
-  ~ProfScope() {
-    if (idx != size_t(-1)) cudaEventRecord(h->events[idx].stop, h->stream);
-  }
-};
-
 int launch_pass_h(foa_dmd *h, int mode, int jcap, const void *x, const double *coef, bool batch,
                   foa_dmd_push_info *info_out) {
   PassArgs a;

@@ -71,6 +71,30 @@ struct foa_dmd {
 };
 
 namespace foa {
+// Record an event pair around a pass launch when profiling.
+struct ProfScope {
+  foa_dmd *h;
+  int kind;
+  double bytes;
+  size_t idx;
+  ProfScope(foa_dmd *h_, int kind_, double bytes_) : h(h_), kind(kind_), bytes(bytes_), idx(size_t(-1)) {
+    if (!h->prof) return;
+    if (h->prof_used == h->events.size()) {
+      EventPair p;
+      cudaEventCreate(&p.start);
+      cudaEventCreate(&p.stop);
+      h->events.push_back(p);
+    }
+    idx = h->prof_used++;
+    h->events[idx].kind = kind;
+    h->events[idx].bytes = bytes;
+    cudaEventRecord(h->events[idx].start, h->stream);
+  }
+  ~ProfScope() {
+    if (idx != size_t(-1)) cudaEventRecord(h->events[idx].stop, h->stream);
+  }
+};
+
 int cuda_status(cudaError_t e);
 int sync_state(foa_dmd *h, foa_dmd_push_info *info);
 int check_device(int *sms);

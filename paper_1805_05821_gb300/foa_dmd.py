@@ -87,6 +87,7 @@ def lib():
             "foa_dmd_profile": (ctypes.c_int, [vp, ctypes.c_int]),
             "foa_dmd_profile_read": (ctypes.c_int, [vp, ctypes.POINTER(foa_dmd_kernel_stats)]),
             "foa_dmd_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32]),
+            "foa_dmd_push_block": (ctypes.c_int, [vp, vp, i32, i64, i32, ctypes.POINTER(foa_dmd_push_info)]),
             "foa_dmd_tuned_geometry": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                                       ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "foa_dmd_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(vp)]),
@@ -273,6 +274,12 @@ def foa_dmd_profile_read(h):
             "total_launches": int(s.total_launches)}
 
 
+def foa_dmd_push_block(h, X, p, ld, block=4, info=True):
+    infos = (foa_dmd_push_info * max(p, 1))() if info else None
+    st = lib().foa_dmd_push_block(h, _ptr(X), int(p), int(ld), int(block), infos)
+    return st, (list(infos)[:p] if info else None)
+
+
 def foa_dmd_autotune(h, cache_path=None, force=False):
     path = str(cache_path).encode() if cache_path else None
     return _check(lib().foa_dmd_autotune(h, path, 1 if force else 0), "foa_dmd_autotune")
@@ -368,6 +375,12 @@ class FoaDMD:
         """X: torch tensor of shape (p, ld) (row t = snapshot t, contiguous, ld >= n)."""
         p, ld = X.shape
         st, infos = foa_dmd_push_batch(self.h, X, p, ld, info)
+        return st, ([i.as_dict() for i in infos] if infos is not None else None)
+
+    def push_block(self, X, block=4, info=True):
+        """X: torch tensor of shape (p, ld) (row t = snapshot t, contiguous, ld >= n)."""
+        p, ld = X.shape
+        st, infos = foa_dmd_push_block(self.h, X, p, ld, block, info)
         return st, ([i.as_dict() for i in infos] if infos is not None else None)
 
     def sync(self):

@@ -147,13 +147,37 @@ def noise(spec, t, r, dtype=np.float64):
 
 
 def snapshots(spec: ModalSpec, dtype=np.float64, N=None, chunk=1 << 20):
-    """The full n x N snapshot matrix (column t = snapshot t), for sizes the host holds."""
+    """The full n x N snapshot matrix (column t = snapshot t), for sizes the host holds.  For the
+    waves kind the spatial factors of a row chunk are formed once and reused for every t; each
+    element goes through the same operations in the same order as rows(), so the values are
+    identical."""
     N = spec.N if N is None else N
     X = np.empty((spec.n, N), dtype=dtype, order="F")
-    for t in range(N):
-        for r0 in range(0, spec.n, chunk):
-            r = np.arange(r0, min(spec.n, r0 + chunk))
-            X[r0:r0 + len(r), t] = rows(spec, t, r, dtype)
+    dt = np.dtype(dtype).type
+    for r0 in range(0, spec.n, chunk):
+        r = np.arange(r0, min(spec.n, r0 + chunk))
+        if spec.kind != "waves":
+            for t in range(N):
+                X[r0:r0 + len(r), t] = rows(spec, t, r, dtype)
+            continue
+        field, idx = _grid_index(spec, r)
+        tabs = [tab.astype(dt) for tab in spec.tables]
+        SR, SI = [], []
+        for m in range(spec.M):
+            sr, si = tabs[0][m, idx[0], 0], tabs[0][m, idx[0], 1]
+            for a in range(1, len(idx)):
+                sr, si = _cmul(sr, si, tabs[a][m, idx[a], 0], tabs[a][m, idx[a], 1])
+            SR.append(sr)
+            SI.append(si)
+        for t in range(N):
+            Tf = spec.T.astype(dt)[:, :, t]
+            acc = np.zeros(r.shape, dtype=dt)
+            for m in range(spec.M):
+                acc = acc + SR[m] * Tf[field, 2 * m]
+                acc = acc + SI[m] * Tf[field, 2 * m + 1]
+            if spec.noise_scale > 0.0:
+                acc = acc + dt(spec.noise_scale) * noise(spec, t, r, dtype)
+            X[r0:r0 + len(r), t] = acc
     return X
 
 

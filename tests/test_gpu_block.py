@@ -1,0 +1,115 @@
+"""GPU parity of the block push (block CGS2 against V + Cholesky QR twice; the block form of the QR
+view) against the oracle's block step on the same blocking.  Tolerances as in test_gpu_push:
+k_max * u_storage * kappa_2(X) normwise on beta and H-bar, against the FP64 oracle on the same
+storage-rounded inputs."""
+import numpy as np
+import pytest
+
+from gpu_util import U, kappa_of, rel, to_device
+from paper_1805_05821_gb300 import synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1805_05821_gb300 import build
+    build.build()
+
+
+def oracle_blocks(Xr, k_max, dt, block, tol=None):
+    """First snapshot alone, then blocks of `block` (the library's blocking for (N-1) % block == 0)."""
+    o = oracle.FoaOracle(Xr.shape[0], k_max, breakdown_tol=tol, storage=dt, form="qr")
+    sts = [o.push(Xr[:, 0])]
+    for s in range(1, Xr.shape[1], block):
+        sts += o.push_block(Xr[:, s:s + block])
+        if o.stopped:
+            break
+    return o, sts
+
+
+def compare(g, o, dt, k_max):
+    q, stopped, H, B = g.state()
+    assert q == o.q and stopped == o.stopped
+    m = o.m
+    kap = kappa_of(o.B, q)
+    tol = k_max * U[dt] * kap
+    eB = rel(B[:q, :q], o.B[:q, :q])
+    eH = rel(H[:m + 1, :m], o.H[:m + 1, :m])
+    assert eB <= tol, (eB, tol)
+    assert eH <= tol, (eH, tol)
+    Vg = g.basis(0, q).double().cpu().numpy().T
+    assert rel(Vg, o.V[:, :q]) <= max(tol, 4 * U[dt])
+    return eB, eH
+
+
+@pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4)])
+def test_block_push_matches_oracle(dt, block):
+    """Waves on a 70^2 grid (n = 4900: ragged last tile), 25 snapshots = 1 + 6 blocks of 4."""
+    spec = synth.config2(41, G=70, N=25)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, dt)
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    g = FoaDMD(spec.n, 25, dt)
+    import torch
+    ld = (spec.n + 7) // 8 * 8  # rows 16-byte aligned for every storage type
+    Xp = torch.zeros((25, ld), dtype=Xd.dtype, device="cuda")
+    Xp[:, :spec.n] = Xd
+    st, infos = g.push_block(Xp, block=block)
+    assert st == 0
+    o, sts = oracle_blocks(Xr, 25, dt, block)
+    assert [i["status"] for i in infos] == ["OK" if s[0] == "ok" else "EBREAKDOWN" for s in sts][:len(infos)]
+    compare(g, o, dt, 25)
+    # the block push agrees with single pushes to the same tolerance
+    g1 = FoaDMD(spec.n, 25, dt)
+    for t in range(25):
+        g1.push(Xd[t])
+    q, _, H1, B1 = g1.state()
+    kap = kappa_of(o.B, q)
+    assert rel(g.state()[3][:q, :q], B1[:q, :q]) <= 25 * U[dt] * kap
+
+
+def test_block_push_breakdown_inside_a_block():
+    """Planted rank-10 map (FP32 storage): snapshot 11 is the second column of the third block of 4;
+    the library commits the block's first column and stops, like the oracle."""
+    spec = synth.config1(0)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f32")
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    g = FoaDMD(spec.n, 32, "f32")
+    st, infos = g.push_block(Xd[:29], block=4)
+    assert st == 5  # EBREAKDOWN
+    assert [i["status"] for i in infos[:10]] == ["OK"] * 10 and infos[10]["status"] == "EBREAKDOWN"
+    assert all(i["status"] == "ESTOPPED" for i in infos[11:])
+    o, sts = oracle_blocks(Xr, 32, "f32", 4)
+    q, stopped, H, B = g.state()
+    assert q == o.q == 10 and stopped
+    assert H[10, 9] == 0.0
+    r = g.eig(0.0)
+    from gpu_util import match
+    d, _ = match(r["lam"], spec.lam)
+    assert d.max() <= 1e-4
+
+
+def test_block_push_on_a_two_pass_handle_and_fp64_refused():
+    import torch
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD, FoaError
+    spec = synth.config2(42, G=48, N=13)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f32")
+    g = FoaDMD(spec.n, 13, "f32", reorth=2)
+    for t in range(5):
+        assert g.push(Xd[t])[0] == 0
+    st, infos = g.push_block(Xd[5:13], block=4)
+    assert st == 0 and g.state()[0] == 13
+    o = oracle.FoaOracle(spec.n, 13, storage="f32", reorth=2)
+    for t in range(5):
+        o.push(Xr[:, t])
+    o.form = "qr"
+    o.push_block(Xr[:, 5:9])
+    o.push_block(Xr[:, 9:13])
+    compare(g, o, "f32", 13)
+    g64 = FoaDMD(1000, 8, "f64")
+    x = torch.zeros((4, 1000), dtype=torch.float64, device="cuda")
+    assert g64.push_block(x, block=4)[0] == 1  # EINVAL
