@@ -3,7 +3,7 @@
 //   BLK_A  (one pass over V)  C1 = V^T X_b and ||psi_k||^2
 //   BLK_B  (one pass over V)  W = X_b - V C1,  C2 = V^T W,  C = C1 + C2
 //   BLK_C  (one pass over V)  W = W - V C2,    G = W^T W, then G = R1^T R1 (Cholesky, FP64)
-//   BLK_Q1 (rows of W only)   W1 = W R1^-1,    G2 = W1^T W1 = R2^T R2, R = R2 R1, breakdown test,
+//   BLK_Q1 (rows of W only)   W1 = W R1^-1 (FP64), G2 = W1^T W1 = R2^T R2, R = R2 R1, breakdown test,
 //                             beta block column [C; R], Hbar columns by forward substitution
 //   BLK_Q2 (rows of W only)   Q = W1 R2^-1 -> V columns j .. j+P-1
 // V is read three times per block instead of three times per snapshot.  The passes share the
@@ -11,7 +11,10 @@
 // shared-memory ring with bulk copies on mbarriers; eight consumer warps make the row sweep
 // (thread <- row pair x column group, P outputs per row) and the column sweep (quarter-warps take
 // four columns, a lane four rows, P products per column); FP32 products, per-CTA FP64 partials
-// and a deterministic two-level cross-CTA reduction.  FP32/BF16 storage.
+// and a deterministic two-level cross-CTA reduction.  FP32/BF16 storage.  From the Gram matrix
+// on, the Cholesky QR works in FP64 (exact products of the FP32 W, W R1^-1 and Q in FP64): stored
+// in FP32, W R1^-1 would carry u_fp32 kappa(W)^2 and lose orthogonality once a block's directions
+// span more than ~sqrt(1/u_fp32) in size.
 #include <cmath>
 #include <cstring>
 
@@ -42,6 +45,7 @@ struct BlockArgs {
   const void *X;        // caller's block: snapshot k at X + k*ldx (storage dtype)
   int64_t ldx;
   float *W;             // P working vectors, each nrows floats
+  double *W64;          // W R1^-1 in FP64 (P x nrows): Cholesky QR keeps FP64 past the Gram matrix
   double *C1, *C;       // j x P coefficients (column k at k*kmax)
   double *partials, *gpart;
   uint32_t *gcount;
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1) block_kernel(const BlockArgs a) {
   const int j = a.j;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *slots = smem;
-  float *ws = reinterpret_cast<float *>(smem + a.off_ws);      // P x R*32 (row sweep results)
+  float *wsb = reinterpret_cast<float *>(smem + a.off_ws);     // 2 x P x R*32 (row sweep results)
   float *cf = reinterpret_cast<float *>(smem + a.off_coef);    // j x P coefficients (row sweep)
   double *dot = reinterpret_cast<double *>(smem + a.off_dot);  // reduction vector
   float *comb = reinterpret_cast<float *>(smem + a.off_comb);  // row-sweep group partials
@@ -243,6 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1) block_kernel(const BlockArgs a) {
     const unsigned char *sbase = slots + size_t(slot) * a.slot_bytes;
     const S *vs = reinterpret_cast<const S *>(sbase);
     const bool bb = kBaseX ? (a.x_aligned && r0 + int64_t(RS) <= a.n) : true;
+    // double buffer: rows of stage s+1 may be finished while slower warps still read stage s's
+    float *ws = wsb + (it & 1) * (P * a.R * kTile);
     // base value k of stage row `row`
     auto base_at = [&](int k, int row) -> float {
       if (bb) {
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) block_kernel(const BlockArgs a) {
 #pragma unroll
           for (int k = 0; k < P; ++k)
 #pragma unroll
-            for (int l = k; l < P; ++l) gram[q++] += double(wv[k] * wv[l]);
+            for (int l = k; l < P; ++l) gram[q++] += double(wv[k]) * double(wv[l]);  // exact products
         }
       };
       const int PR = RS >> 1;
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(kThreads, 1) block_kernel(const BlockArgs a) {
   }
 }
 
-// W1 = W R1^-1 on the leading m1 columns, G2 = W1^T W1 (per CTA partials), and in the last CTA:
+// W1 = W R1^-1 on the leading m1 columns (FP64), G2 = W1^T W1 (per CTA partials), and in the last CTA:
 // R2, R = R2 R1, the breakdown test, the beta block column, the Hbar columns, the device state.
 template <int P>
 __global__ void __launch_bounds__(256) blockq1_kernel(BlockArgs a, foa_dmd_push_info *info_out) {
@@ -446,11 +452,7 @@ __global__ void __launch_bounds__(256) blockq1_kernel(BlockArgs a, foa_dmd_push_
       w1[c] = (c < m1) ? t / R1[c + c * P] : 0.0;
     }
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-      const float f = float(w1[c]);
-      a.W[int64_t(c) * a.nrows + r] = f;
-      w1[c] = double(f);  // the stored value
-    }
+    for (int c = 0; c < P; ++c) a.W64[int64_t(c) * a.nrows + r] = w1[c];
 #pragma unroll
     for (int k = 0; k < P; ++k)
 #pragma unroll
@@ -610,7 +612,7 @@ __global__ void blockq2_kernel(BlockArgs a) {
     double q[P];
 #pragma unroll
     for (int c = 0; c < P; ++c) {
-      double t = a.W[int64_t(c) * a.nrows + r];
+      double t = a.W64[int64_t(c) * a.nrows + r];
 #pragma unroll
       for (int k = 0; k < c; ++k) t -= q[k] * R2[k + c * P];
       q[c] = t / R2[c + c * P];
@@ -645,6 +647,7 @@ namespace {
 
 struct BlockWork {
   float *W = nullptr;
+  double *W64 = nullptr;
   double *C1 = nullptr, *C = nullptr;
   BlockState *bs = nullptr;
   foa_dmd_push_info *info = nullptr;
@@ -692,7 +695,7 @@ bool block_geom(const foa_dmd *h, int P, int j, BlockArgs &a, int &grid) {
   auto up = [](int64_t v, int64_t al) { return (v + al - 1) / al * al; };
   const int64_t base_stride = up(int64_t(R) * kTile * 4, 128);
   const int64_t slot = up(R * tile_bytes, 128) + P * base_stride;
-  const int64_t other = up(int64_t(P) * R * kTile * 4, 128) + up(int64_t(j) * P * 4, 16) +
+  const int64_t other = up(2 * int64_t(P) * R * kTile * 4, 128) + up(int64_t(j) * P * 4, 16) +
                         up(int64_t(j * P + P * P + P) * 8, 16) + int64_t(512) * P * 4 +
                         int64_t(kConsumers) * (P * (P + 1) / 2 > P ? P * (P + 1) / 2 : P) * 8 + 2 * kMaxSlots * 8 + 64;
   int slots = int((int64_t(200) * 1024 - other) / slot);
@@ -705,7 +708,7 @@ bool block_geom(const foa_dmd *h, int P, int j, BlockArgs &a, int &grid) {
   a.base_stride = int(base_stride);
   int64_t off = slot * slots;
   a.off_ws = int(off);
-  off += up(int64_t(P) * R * kTile * 4, 128);
+  off += up(2 * int64_t(P) * R * kTile * 4, 128);
   a.off_coef = int(off);
   off += up(int64_t(j) * P * 4, 16);
   a.off_dot = int(off);
@@ -744,6 +747,7 @@ int enqueue_block(foa_dmd *h, BlockWork &bw, const void *X, int64_t ldx, foa_dmd
   a.X = X;
   a.ldx = ldx;
   a.W = bw.W;
+  a.W64 = bw.W64;
   a.C1 = bw.C1;
   a.C = bw.C;
   a.partials = h->partials;
@@ -798,6 +802,7 @@ extern "C" int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, in
   if (h->stopped_host) return FOA_DMD_ESTOPPED;
   BlockWork bw;
   cudaError_t e = cudaMalloc(&bw.W, size_t(kMaxP) * h->nrows * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&bw.W64, size_t(kMaxP) * h->nrows * 8);
   if (e == cudaSuccess) e = cudaMalloc(&bw.C1, size_t(kMaxP) * h->kmax * 8);
   if (e == cudaSuccess) e = cudaMalloc(&bw.C, size_t(kMaxP) * h->kmax * 8);
   if (e == cudaSuccess) e = cudaMalloc(&bw.bs, sizeof(BlockState));
@@ -867,6 +872,7 @@ extern "C" int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, in
   }
   cudaStreamSynchronize(h->stream);
   cudaFree(bw.W);
+  cudaFree(bw.W64);
   cudaFree(bw.C1);
   cudaFree(bw.C);
   cudaFree(bw.bs);

@@ -1,7 +1,8 @@
 // Streaming passes over the basis V for one modified-FOA push (Alg. 1 steps 9-15, Alg. 4
-// steps 17-23).  One templated kernel serves four pass kinds:
+// steps 17-23).  The pass kinds:
 //
 //   PASS_A      w = (x - V beta_pre) / beta_jj  (step 9),  h = V^T w         (step 10), ||x||^2
+//               (QR view: w = x)
 //   PASS_B      w = w - V h                     (step 11), s = V^T w         (step 12)
 //   PASS_C      w = w - V s                     (step 14), ||w||^2           (step 15)
 //   PASS_FIRST  ||x||^2 of the first snapshot (Alg. 1 step 2)
@@ -12,20 +13,18 @@
 // another (32 contiguous elements per column), so the leading j columns of a tile are one
 // contiguous block of 32*j elements.  A pipeline stage is R consecutive tiles; a producer warp
 // fetches each stage's tiles (and the 32R-row slice of x or w) into a shared-memory ring with
-// one-dimensional bulk async copies completing on mbarriers, and eight consumer warps make two
+// one-dimensional bulk async copies completing on mbarriers, and the consumer warps make two
 // sweeps over the staged block, so V is read from HBM exactly once per pass:
-//   sweep 1 (row-local GEMV-N): thread <- row (x column group), FP32 FMA over blocks of 32
-//           columns folded into FP64, giving the new w for the row;
-//   sweep 2 (GEMV-T split over rows): warp <- columns {warp, warp+8, ...}, lane <- row, one
-//           register accumulator per owned column, flushed with a warp reduction into FP64
-//           every 32 products per lane.
-// Each CTA leaves its FP64 partial vector in global memory; the last CTA of every group of 8
-// CTAs (atomic ticket) sums its group in CTA order, and the last group sums the group partials
-// in group order, so the reduction is deterministic.  That last CTA then applies the scalar
-// part of the step (h, s, h+s, h_{j+1,j}, the beta and H-bar columns, the breakdown test).
+//   sweep 1 (row-local GEMV-N): the new w of every row of the stage;
+//   sweep 2 (GEMV-T split over rows): the column dots, one register accumulator per owned column,
+//           folded into FP64 every 32 products per lane.
+// pass_kernel (this file) runs pass C and PASS_FIRST for every storage type and passes A, B, B2
+// for FP64 storage, with all eight consumer warps on sweep 1 and then on sweep 2.  For FP32/BF16
+// storage passes A, B and B2 run in pass_ws_kernel (pass_ws.cuh), which puts the two sweeps on
+// different warps so that they overlap across stages.  Both end in pass_epilogue.
 //
 // Every wait is bounded; a timeout records FOA_DMD_ETIMEOUT in the device state and the CTA
-// drains its outstanding copies before it returns.
+// stops waiting (its results are discarded by the host).
 #pragma once
 #include "internal.cuh"
 

@@ -113,3 +113,32 @@ def test_block_push_on_a_two_pass_handle_and_fp64_refused():
     g64 = FoaDMD(1000, 8, "f64")
     x = torch.zeros((4, 1000), dtype=torch.float64, device="cuda")
     assert g64.push_block(x, block=4)[0] == 1  # EINVAL
+
+
+def test_block_push_wide_basis_fields():
+    """The fields workload's structure at a small grid (4 x 16^3, n = 16384), N = 160 in blocks of 4:
+    past j = 128 a pipeline stage is one 32-row tile and the row sweep splits the columns into 16
+    groups.  Against the oracle's block step; leading Ritz values against the planted ones."""
+    import torch
+    from scipy.optimize import linear_sum_assignment
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    spec = synth.config5(0, G=16, N=160)
+    X = synth.snapshots(spec, np.float32).astype(np.float64)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.T)).float().cuda()
+    g = FoaDMD(spec.n, 160, "f32", breakdown_tol=1e-12)
+    st, _ = g.push_block(Xd, block=4)
+    assert st == 0
+    o = oracle.FoaOracle(spec.n, 160, breakdown_tol=1e-12, storage="f32", form="qr")
+    o.push(X[:, 0])
+    for s in range(1, 160, 4):
+        o.push_block(X[:, s:s + 4])
+    q, stopped, H, B = g.state()
+    assert q == o.q == 160
+    Vg = g.basis(0, q).double().cpu().numpy().T
+    orth = np.linalg.norm(np.eye(q) - Vg.T @ Vg, 2)
+    assert orth <= 1e-4, orth
+    r = g.eig(-1.0)
+    lam = r["lam"][:32]
+    D = np.abs(lam[:, None] - spec.lam[None, :])
+    ri, ci = linear_sum_assignment(D)
+    assert np.max(D[ri, ci] / np.abs(spec.lam[ci])) <= 1e-5
