@@ -295,8 +295,9 @@ int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld, i
  * kind the handle's options use (A/B/C, or the two passes of reorth = 2) and every j bucket up to
  * k_max (upper ends 8, 16, 32, 64, 128, 192, 256, 320, 384, 448, 512), times each candidate
  * (V bytes per pipeline stage 16/32/64 KB x V bytes in flight per CTA 64/96/144/192 KB x one or two
- * CTAs per SM) on the handle's own buffers, over a prefix of V of about 2 GB, median of three
- * launches, and keeps the fastest; later pushes of the handle launch with it.
+ * CTAs per SM x, for the FP32/BF16 passes with column dots, the register-held or the shared-
+ * memory form of the stage) on the handle's own buffers, over a prefix of V of about 2 GB, median
+ * of three launches, and keeps the fastest; later pushes of the handle launch with it.
  *   cache_path: NULL, or a text file.  Choices found there for (device arch, dtype, floor(log2 n),
  *               kind, bucket) are used without timing; new choices are appended.
  *   flags:      bit 0 = time again even where the cache has a choice.
@@ -304,11 +305,12 @@ int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld, i
  * V, H-bar, beta and the working vector, and clears them again before returning.  Errors:
  * EINVAL (q != 0), ENOMEM, ECUDA, ETIMEOUT.  foa_dmd_tuned_geometry reports the geometry a pass
  * of kind (0 A, 1 B, 2 C, 3 lagged first pass, 4 second pass of the two-pass push) at basis size j
- * launches with, and whether it was tuned (*tuned = 1) or is the default.
+ * launches with (variant 0: register-held stage where it fits, 1: shared-memory stage), and whether
+ * it was tuned (*tuned = 1) or is the default.
  */
 int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t flags);
 int foa_dmd_tuned_geometry(foa_dmd_t *h, int32_t kind, int32_t j, int64_t *stage_bytes, int64_t *inflight_bytes,
-                           int32_t *ctas_per_sm, int32_t *tuned);
+                           int32_t *ctas_per_sm, int32_t *variant, int32_t *tuned);
 
 /* Pinned host memory for foa_dmd_push_host (cudaHostAlloc / cudaFreeHost). */
 int foa_dmd_host_alloc(size_t bytes, void **ptr);

@@ -43,7 +43,7 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   const int64_t slot_bytes = vpart + bpart;
   const int64_t ws_bytes = align_up(2 * int64_t(R) * kTile * cs, 128);
   const int64_t vnew_bytes = lag ? align_up(2 * int64_t(R) * kTile * cs, 128) : 0;  // double-buffered
-  const int64_t cf_bytes = align_up(int64_t(jcap + 8) * cs, 16);
+  const int64_t cf_bytes = align_up(int64_t(jcap + 96) * cs, 16);  // room for the fused pass's padding
   const int64_t cf2_bytes = lag ? cf_bytes : 0;
   const int64_t comb_bytes = lag ? 2 * kConsumers * 8 : kConsumers * 8;
   const int64_t other = ws_bytes + vnew_bytes + cf_bytes + cf2_bytes + align_up(int64_t(jcap + 2) * 8, 16) +
@@ -61,6 +61,7 @@ bool make_pass_geom(const Geometry &g, int dtype, int mode, int jcap, int64_t n,
   if (slots < 2) return false;
   a.R = R;
   a.slots = slots;
+  a.variant = g.variant;
   a.slot_bytes = int(slot_bytes);
   a.base_off = int(vpart);
   a.base2_off = lag ? int(vpart + align_up(int64_t(R) * kTile * s, 128)) : 0;

@@ -13,6 +13,7 @@ struct Geometry {
   int64_t smem_budget2 = 112 * 1024;   // ... when two CTAs share an SM
   int64_t inflight_bytes = 96 * 1024;  // bytes of V each CTA keeps in flight
   int max_ctas_per_sm = 2;
+  int variant = 0;  // FP32/BF16 passes A, B, B2: 0 = register-held stage where it fits, 1 = shared memory
 };
 
 struct EventPair {

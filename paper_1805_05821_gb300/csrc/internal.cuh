@@ -81,6 +81,7 @@ struct PassArgs {
   int32_t off_ws, off_coef, off_dot, off_comb, off_norm, off_bar, smem_total;
   int32_t base2_off;     // PASS_A2 / PASS_FIN: w' slice within a slot
   int32_t off_vnew, off_coef2;
+  int32_t variant;       // FP32/BF16 passes A, B, B2: 0 = stage in registers where it fits, 1 = shared memory
 };
 
 // ------------------------------------------------------------------------------------------

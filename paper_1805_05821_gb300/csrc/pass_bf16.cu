@@ -1,6 +1,7 @@
 // Instantiations of the streaming-pass kernel for __nv_bfloat16 storage.
 #include "pass.cuh"
 #include "pass_ws.cuh"
+#include "pass_fused.cuh"
 
 namespace foa {
 
@@ -31,8 +32,25 @@ static cudaError_t launch_ws_one(const PassArgs &a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// wide-basis stages (one or two tiles) held in registers: pass_fused_kernel
+template <int MODE, int FC>
+static cudaError_t launch_fused_one(const PassArgs &a, int grid, cudaStream_t s) {
+  auto k = pass_fused_kernel<__nv_bfloat16, MODE, FC>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  k<<<grid, kThreads, a.smem_total, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int MODE>
 static cudaError_t launch_ws(int nc, const PassArgs &a, int grid, cudaStream_t s) {
+  const int fc = fused_columns(a);
+  if (fc == 16) return launch_fused_one<MODE, 16>(a, grid, s);
+  if (fc == 24) return launch_fused_one<MODE, 24>(a, grid, s);
   switch (nc) {
     case 8: return launch_ws_one<MODE, 8>(a, grid, s);
     case 16: return launch_ws_one<MODE, 16>(a, grid, s);

@@ -71,7 +71,7 @@ __global__ void tune_state_kernel(DevState *st, int j, int pending) {
 
 struct Candidate {
   int64_t stage, inflight;
-  int ctas;
+  int ctas, variant;
 };
 
 const int kKindMode[kTuneKinds] = {PASS_A, PASS_B, PASS_C, PASS_A2, PASS_B2};
@@ -89,16 +89,16 @@ int log2_floor(int64_t n) {
   return l;
 }
 
-// Cache lines: "foa_dmd_tune arch dtype log2n kind bucket stage inflight ctas ms"
+// Cache lines: "foa_dmd_tune arch dtype log2n kind bucket stage inflight ctas variant ms"
 void load_cache(foa_dmd *h, const char *path, int arch, int nb) {
   FILE *f = fopen(path, "r");
   if (!f) return;
   char tag[32];
-  int a, dt, l2, kind, b, ctas;
+  int a, dt, l2, kind, b, ctas, variant;
   long long stage, inflight;
   double ms;
-  while (fscanf(f, "%31s %d %d %d %d %d %lld %lld %d %lf", tag, &a, &dt, &l2, &kind, &b, &stage, &inflight, &ctas,
-                &ms) == 10) {
+  while (fscanf(f, "%31s %d %d %d %d %d %lld %lld %d %d %lf", tag, &a, &dt, &l2, &kind, &b, &stage, &inflight, &ctas,
+                &variant, &ms) == 11) {
     if (strcmp(tag, "foa_dmd_tune") != 0 || a != arch || dt != h->dtype || l2 != nb) continue;
     if (kind < 0 || kind >= kTuneKinds || b < 0 || b >= kTuneBuckets) continue;
     if (stage < 4096 || stage > (1 << 20) || inflight < 4096 || inflight > (1 << 20) || ctas < 1 || ctas > 2) continue;
@@ -106,6 +106,7 @@ void load_cache(foa_dmd *h, const char *path, int arch, int nb) {
     g.stage_bytes = stage;
     g.inflight_bytes = inflight;
     g.max_ctas_per_sm = ctas;
+    g.variant = (variant == 1) ? 1 : 0;
     h->tuned[kind][b] = g;
     h->tuned_ok[kind][b] = true;
   }
@@ -155,7 +156,8 @@ extern "C" int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t fl
   std::vector<Candidate> cands;
   for (int64_t st : {16384, 32768, 65536})
     for (int64_t inf : {65536, 98304, 147456, 196608})
-      for (int c : {1, 2}) cands.push_back({st, inf, c});
+      for (int c : {1, 2})
+        for (int v : {0, 1}) cands.push_back({st, inf, c, v});
   const int sms = h->sms - (h->opts.indicator_every > 0 ? 1 : 0);
   FILE *cache = (cache_path && *cache_path) ? fopen(cache_path, "a") : nullptr;
   for (int k = 0; k < kTuneKinds && rc == FOA_DMD_OK; ++k) {
@@ -180,12 +182,15 @@ extern "C" int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t fl
         g.stage_bytes = c.stage;
         g.inflight_bytes = c.inflight;
         g.max_ctas_per_sm = c.ctas;
+        g.variant = c.variant;
+        // the register-held form exists for the FP32/BF16 passes with column dots only
+        if (c.variant == 1 && (h->dtype == FOA_DMD_F64 || mode == PASS_C)) continue;
         PassArgs a;
         memset(&a, 0, sizeof(a));
         int grid = 0;
         if (!make_pass_geom(g, h->dtype, mode, j, n_t, int(tiles), sms, a, grid)) continue;
         char key[96];
-        snprintf(key, sizeof(key), "%d/%d/%d/%d", a.R, a.slots, grid, a.smem_total);
+        snprintf(key, sizeof(key), "%d/%d/%d/%d/%d", a.R, a.slots, grid, a.smem_total, c.variant);
         bool dup = false;
         for (auto &q : seen) dup = dup || q == key;
         if (dup) continue;  // same launch as an earlier candidate
@@ -245,8 +250,9 @@ extern "C" int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t fl
       h->tuned[k][b] = bestg;
       h->tuned_ok[k][b] = true;
       if (cache)
-        fprintf(cache, "foa_dmd_tune %d %d %d %d %d %lld %lld %d %.6f\n", arch, h->dtype, nb, k, b,
-                (long long)bestg.stage_bytes, (long long)bestg.inflight_bytes, bestg.max_ctas_per_sm, best);
+        fprintf(cache, "foa_dmd_tune %d %d %d %d %d %lld %lld %d %d %.6f\n", arch, h->dtype, nb, k, b,
+                (long long)bestg.stage_bytes, (long long)bestg.inflight_bytes, bestg.max_ctas_per_sm, bestg.variant,
+                best);
     }
   }
   if (cache) fclose(cache);
@@ -269,12 +275,14 @@ extern "C" int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t fl
 }
 
 extern "C" int foa_dmd_tuned_geometry(foa_dmd_t *h, int32_t kind, int32_t j, int64_t *stage_bytes,
-                                      int64_t *inflight_bytes, int32_t *ctas_per_sm, int32_t *tuned) {
+                                      int64_t *inflight_bytes, int32_t *ctas_per_sm, int32_t *variant,
+                                      int32_t *tuned) {
   if (!h || kind < 0 || kind >= kTuneKinds || j < 1) return FOA_DMD_EINVAL;
   const Geometry &g = geom_for(h, kKindMode[kind], j);
   if (stage_bytes) *stage_bytes = g.stage_bytes;
   if (inflight_bytes) *inflight_bytes = g.inflight_bytes;
   if (ctas_per_sm) *ctas_per_sm = g.max_ctas_per_sm;
+  if (variant) *variant = g.variant;
   if (tuned) *tuned = h->tuned_ok[kind][tune_bucket(j)] ? 1 : 0;
   return FOA_DMD_OK;
 }

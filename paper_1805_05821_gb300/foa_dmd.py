@@ -89,7 +89,7 @@ def lib():
             "foa_dmd_autotune": (ctypes.c_int, [vp, ctypes.c_char_p, i32]),
             "foa_dmd_push_block": (ctypes.c_int, [vp, vp, i32, i64, i32, ctypes.POINTER(foa_dmd_push_info)]),
             "foa_dmd_tuned_geometry": (ctypes.c_int, [vp, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
-                                                      ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+                                                      ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
             "foa_dmd_host_alloc": (ctypes.c_int, [ctypes.c_size_t, ctypes.POINTER(vp)]),
             "foa_dmd_host_free": (ctypes.c_int, [vp]),
             "foa_dmd_batch_create": (ctypes.c_int, [i32, ctypes.POINTER(i64), ctypes.POINTER(i32), i32,
@@ -287,10 +287,11 @@ def foa_dmd_autotune(h, cache_path=None, force=False):
 
 def foa_dmd_tuned_geometry(h, kind, j):
     st, inf = ctypes.c_int64(), ctypes.c_int64()
-    ctas, tuned = ctypes.c_int32(), ctypes.c_int32()
+    ctas, variant, tuned = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().foa_dmd_tuned_geometry(h, int(kind), int(j), ctypes.byref(st), ctypes.byref(inf), ctypes.byref(ctas),
-                                        ctypes.byref(tuned)), "foa_dmd_tuned_geometry")
-    return {"stage_bytes": st.value, "inflight_bytes": inf.value, "ctas_per_sm": ctas.value, "tuned": bool(tuned.value)}
+                                        ctypes.byref(variant), ctypes.byref(tuned)), "foa_dmd_tuned_geometry")
+    return {"stage_bytes": st.value, "inflight_bytes": inf.value, "ctas_per_sm": ctas.value,
+            "variant": variant.value, "tuned": bool(tuned.value)}
 
 
 def foa_dmd_host_alloc(nbytes):

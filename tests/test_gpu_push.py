@@ -223,3 +223,16 @@ def test_waves_2d_full_size(dt):
     assert len(infos) == len(sts)
     eB, eH, kap = compare_state(g, o, dt, 200)
     print(dt, "kappa", kap, "errB", eB, "errH", eH)
+
+
+@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("bf16", 1), ("f32", 2)])
+def test_wide_basis_register_stage(dt, reorth):
+    """N = 160 on a 96^2 waves grid (n = 9216): past j = 64 a pipeline stage is one or two 32-row
+    tiles and the FP32/BF16 passes with column dots hold the stage in registers."""
+    spec = synth.config2(6, G=96, N=160)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, dt)
+    g, infos = run_gpu(Xd, spec.n, 160, dt, reorth=reorth, breakdown_tol=1e-12)
+    o, sts = run_oracle(Xr, 160, dt, tol=1e-12, reorth=reorth)
+    assert len(infos) == len(sts) == 160
+    compare_state(g, o, dt, 160)
