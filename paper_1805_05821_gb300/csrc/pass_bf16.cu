@@ -42,7 +42,7 @@ static cudaError_t launch_fused_one(const PassArgs &a, int grid, cudaStream_t s)
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  k<<<grid, kThreads, a.smem_total, s>>>(a);
+  k<<<grid, kConsumers, a.smem_total, s>>>(a);  // no producer warp
   return cudaGetLastError();
 }
 

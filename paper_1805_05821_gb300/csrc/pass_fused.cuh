@@ -3,13 +3,15 @@
 //
 // A thread owns a fixed pair of adjacent rows of every stage and a fixed group of columns
 // (16 or 32 threads share a column group).  Per stage it loads its V fragment (2 rows x FC
-// columns) into registers once and releases the shared-memory slot at once, so the producer
-// refills it while the stage is being computed; then, from the registers,
+// columns) into registers once; from the registers,
 //   row sweep:     partial sums of the GEMV-N for its two rows, combined across the column groups
 //                  through shared memory, the new w of the stage's rows (as pass_kernel);
 //   column sweep:  its columns' dot products with the two new w values, one FP32 accumulator
 //                  per column, folded every 16 stages (32 products per lane) by a shuffle tree
 //                  over the threads of the column group into the CTA's FP64 dot vector.
+// There is no producer warp: the CTA is the eight compute warps (two CTAs of 256 threads per SM,
+// up to 128 registers a thread for the fragment), and one elected thread refills a ring slot as
+// soon as the first CTA barrier of the stage shows every thread holding its fragment.
 // The cross-CTA reduction and the scalar step are pass_epilogue.
 #pragma once
 #include "pass.cuh"
@@ -27,7 +29,7 @@ inline int fused_columns(const PassArgs &a) {
 }
 
 template <typename S, int MODE, int FC>
-__global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two CTAs of 288 threads per SM
+__global__ void __launch_bounds__(kConsumers, 2) pass_fused_kernel(const PassArgs a) {
   static_assert(sizeof(typename Compute<S>::T) == 4, "FP32/BF16 storage only");
   static_assert(MODE == PASS_A || MODE == PASS_B || MODE == PASS_B2, "passes with column dots only");
   constexpr bool kBaseX = (MODE == PASS_A);
@@ -41,7 +43,6 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
   if (j < 1 || j > a.jcap) return;
 
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
   unsigned char *slots = smem;
   float *ws = reinterpret_cast<float *>(smem + a.off_ws);      // w of the stage's rows
   float *cf = reinterpret_cast<float *>(smem + a.off_coef);    // coefficients, zero padded
@@ -49,16 +50,12 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
   float *comb = reinterpret_cast<float *>(smem + a.off_comb);  // row-sweep group partials
   double *nrm = reinterpret_cast<double *>(smem + a.off_norm);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + a.off_bar);
-  uint64_t *empty = full + kMaxSlots;
-  volatile int *sflag = reinterpret_cast<volatile int *>(empty + kMaxSlots);  // [0] abort [2] last
+  volatile int *sflag = reinterpret_cast<volatile int *>(full + 2 * kMaxSlots);  // [0] abort [2] last
 
   const bool qr_a = (MODE == PASS_A) && a.form != 0;
   const float cscale = (MODE == PASS_A && !qr_a) ? float(st->inv_bjj) : 1.f;
   if (tid == 0) {
-    for (int i = 0; i < a.slots; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kWarps);
-    }
+    for (int i = 0; i < a.slots; ++i) mbar_init(&full[i], 1);
     sflag[0] = 0;
     sflag[2] = 0;
     mbar_fence_init();
@@ -68,43 +65,38 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
   const int G1 = kConsumers / PF;                     // 16 or 8
   const int cpg = (((j + G1 - 1) / G1) + 3) & ~3;     // <= FC (host check)
   // coefficients zero-padded past every group's FC-wide window (G1*cpg + FC <= j + 88 < jcap + 96)
-  for (int c = tid; c < G1 * cpg + FC; c += kThreads) cf[c] = c < j ? static_cast<float>(a.coef[c]) : 0.f;
-  for (int c = tid; c <= j; c += kThreads) dot[c] = 0.0;
+  for (int c = tid; c < G1 * cpg + FC; c += kConsumers) cf[c] = c < j ? static_cast<float>(a.coef[c]) : 0.f;
+  for (int c = tid; c <= j; c += kConsumers) dot[c] = 0.0;
   __syncthreads();
 
   const S *Vg = static_cast<const S *>(a.V);
   const int64_t tile_elems = int64_t(a.kmax) * kTile;
   const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
 
-  if (warp == kWarps) {
-    // ---------------------------------------------------------------- producer warp
-    if (lane == 0) {
-      const BaseT *baseg = kBaseX ? static_cast<const BaseT *>(a.x) : static_cast<const BaseT *>(a.w);
-      int it = 0;
-      for (int s = blockIdx.x; s < a.nstages; s += gridDim.x, ++it) {
-        const int slot = it % a.slots;
-        if (it >= a.slots && !mbar_wait(&empty[slot], ((it / a.slots) - 1) & 1)) {
-          sflag[0] = 1;
-          atomicExch(&st->err, FOA_DMD_ETIMEOUT);
-          break;
-        }
-        if (sflag[0]) break;
-        const int t0 = s * a.R;
-        const int nt = min(a.R, a.ntiles - t0);
-        const int64_t r0 = int64_t(t0) * kTile;
-        const bool base_bulk = kBaseX ? (a.x_aligned && r0 + int64_t(nt) * kTile <= a.n) : true;
-        const uint32_t bbytes = base_bulk ? uint32_t(nt) * kTile * sizeof(BaseT) : 0u;
-        unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
-        mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
-        for (int k = 0; k < nt; ++k)
-          bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
-        if (bbytes) bulk_g2s(dst + a.base_off, baseg + r0, bbytes, &full[slot]);
-      }
+  // one elected thread issues the copies of a stage: R whole tiles of V and the stage's slice of x
+  // (pass A) or w; a partial x slice (unaligned x, ragged end) is read from global memory instead
+  const BaseT *bg = kBaseX ? static_cast<const BaseT *>(a.x) : static_cast<const BaseT *>(a.w);
+  constexpr int kIssuer = kConsumers - 1;  // not one of the row finishers (tid < 64)
+  auto issue = [&](int slot, int s) {
+    const int t0 = s * a.R;
+    const int nt = min(a.R, a.ntiles - t0);
+    const int64_t r0 = int64_t(t0) * kTile;
+    const bool base_bulk = kBaseX ? (a.x_aligned && r0 + int64_t(nt) * kTile <= a.n) : true;
+    const uint32_t bbytes = base_bulk ? uint32_t(nt) * kTile * sizeof(BaseT) : 0u;
+    unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
+    mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
+    for (int k = 0; k < nt; ++k)
+      bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
+    if (bbytes) bulk_g2s(dst + a.base_off, bg + r0, bbytes, &full[slot]);
+  };
+  if (tid == kIssuer)
+    for (int k = 0; k < a.slots; ++k) {
+      const int s = blockIdx.x + k * gridDim.x;
+      if (s >= a.nstages) break;
+      issue(k, s);
     }
-    return;
-  }
 
-  // ------------------------------------------------------------------ consumer warps
+  // ------------------------------------------------------------------ compute
   const int g = tid / PF, pr = tid % PF;
   const int c0 = g * cpg;
   const int nc = max(0, min(j, c0 + cpg) - c0);       // this thread's columns
@@ -132,7 +124,6 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
   };
   int since_flush = 0;
   int it = 0;
-  const BaseT *bg = kBaseX ? static_cast<const BaseT *>(a.x) : static_cast<const BaseT *>(a.w);
   for (int s = blockIdx.x; s < a.nstages; s += gridDim.x, ++it) {
     const int slot = it % a.slots;
     if (!sflag[0] && !mbar_wait(&full[slot], (it / a.slots) & 1)) {
@@ -146,7 +137,7 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
     const unsigned char *sbase = slots + size_t(slot) * a.slot_bytes;
     const S *vs = reinterpret_cast<const S *>(sbase);
     const bool base_bulk = kBaseX ? (a.x_aligned && r0 + int64_t(RS) <= a.n) : true;
-    // ---------------- the thread's V fragment and its finish row's base value, then release
+    // ---------------- the thread's V fragment and its finish row's base value
     const int row = 2 * pr;
     const bool has_rows = row < RS;
     float2 v[FC];
@@ -160,8 +151,6 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
       if (base_bulk) base = to_c(reinterpret_cast<const BaseT *>(sbase + a.base_off)[tid]);
       else base = (r0 + tid < a.n) ? float(to_c(bg[r0 + tid])) : 0.f;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[slot]);  // the stage lives in registers from here on
     // ---------------- row sweep from registers
     if (!qr_a) {
       float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
@@ -176,7 +165,11 @@ __global__ void __maxnreg__(112) pass_fused_kernel(const PassArgs a) {  // two C
       comb[g * (2 * PF) + row] = a0 + a1;
       comb[g * (2 * PF) + row + 1] = b0 + b1;
     }
-    named_bar_sync(1, kConsumers);
+    named_bar_sync(1, kConsumers);  // every thread holds its fragment: the slot is free
+    if (tid == kIssuer && !sflag[0]) {
+      const int sn = s + a.slots * gridDim.x;
+      if (sn < a.nstages) issue(slot, sn);
+    }
     if (tid < RS) {
       float acc = 0.f;
       if (!qr_a)
