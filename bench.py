@@ -157,7 +157,7 @@ def measured_peak():
 
 def pass_kernel_hash():
     h = hashlib.sha1()
-    for f in ("pass.cuh", "pass_ws.cuh", "pass_fused.cuh", "lag.cuh", "internal.cuh"):
+    for f in ("pass.cuh", "pass_ws.cuh", "pass_fused.cuh", "lag.cuh", "lag_ws.cuh", "lag_fused.cuh", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1805_05821_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -331,7 +331,7 @@ def main():
             "frac": achieved / peak if achieved else None,
             "traffic": (ratio * pass_bytes / pass_launches) if (ratio and pass_launches) else None,
             "kernel": ("streaming passes over V: pass_fused_kernel or pass_ws_kernel (A, B) + pass_kernel (C)" if args.reorth == 1 else
-                       "streaming passes over V: lag_ws_kernel (A2) + pass_fused_kernel or pass_ws_kernel (B2)"),
+                       "streaming passes over V: lag_fused_kernel or lag_ws_kernel (A2) + pass_fused_kernel or pass_ws_kernel (B2)"),
             "algorithmic_bytes_per_launch": pass_bytes / pass_launches if pass_launches else None,
             "avg_launch_ms": pass_ms / pass_launches if pass_launches else None,
             "share_of_step": pass_ms / (secs * 1e3) if secs > 0 else None,

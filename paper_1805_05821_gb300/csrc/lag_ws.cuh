@@ -14,6 +14,71 @@ constexpr int kLagRowWarps = 4;
 constexpr int kLagColWarps = kWarps - kLagRowWarps;
 constexpr int kLagRowThreads = kLagRowWarps * 32;
 
+// Cross-CTA reduction of the lagged first pass (as pass_epilogue), then h and ||x|| of the push.
+// On entry every thread has added its column partials into dot[0..j) and stored its norm partial
+// in nrm[tid]; pend_part, when given, holds eight per-warp partials of the appended column's dot,
+// written before the call and summed here in a fixed order into dot[jt].
+__device__ __forceinline__ void lag_epilogue(const PassArgs &a, DevState *st, double *dot, double *nrm,
+                                             const double *pend_part, volatile int *sflag, const int j,
+                                             const int jt, const int tid) {
+  named_bar_sync(1, kConsumers);
+  if (tid == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kConsumers; ++i) t += nrm[i];
+    dot[j] = t;
+    if (pend_part) {
+      double p = 0.0;
+      for (int w = 0; w < kWarps; ++w) p += pend_part[w];
+      dot[jt] = p;
+    }
+  }
+  named_bar_sync(1, kConsumers);
+  const int len = j + 1;
+  double *mypart = a.partials + size_t(blockIdx.x) * (a.kmax + 1);
+  for (int c = tid; c < len; c += kConsumers) mypart[c] = dot[c];
+  __threadfence();
+  named_bar_sync(1, kConsumers);
+  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
+  const int grp = blockIdx.x / kGroup;
+  const int gfirst = grp * kGroup;
+  const int gsize = min(kGroup, int(gridDim.x) - gfirst);
+  if (tid == 0) {
+    const unsigned t = atomicAdd(&a.gcount[grp], 1u);
+    sflag[2] = (t == unsigned(gsize - 1)) ? 1 : 0;
+  }
+  named_bar_sync(1, kConsumers);
+  if (!sflag[2]) return;
+  __threadfence();
+  double *gp = a.gpart + size_t(grp) * (a.kmax + 1);
+  for (int c = tid; c < len; c += kConsumers) {
+    double t = 0.0;
+    for (int bq = 0; bq < gsize; ++bq) t += __ldcg(a.partials + size_t(gfirst + bq) * (a.kmax + 1) + c);
+    gp[c] = t;
+  }
+  __threadfence();
+  named_bar_sync(1, kConsumers);
+  if (tid == 0) {
+    a.gcount[grp] = 0u;
+    const unsigned t = atomicAdd(&st->ticket[PASS_A2], 1u);
+    sflag[2] = (t == unsigned(ngroups - 1)) ? 1 : 0;
+  }
+  named_bar_sync(1, kConsumers);
+  if (!sflag[2]) return;
+  __threadfence();
+  for (int c = tid; c < len; c += kConsumers) {
+    double t = 0.0;
+    for (int g = 0; g < ngroups; ++g) t += __ldcg(a.gpart + size_t(g) * (a.kmax + 1) + c);
+    dot[c] = t;
+  }
+  if (tid == 0) st->ticket[PASS_A2] = 0u;
+  named_bar_sync(1, kConsumers);
+  for (int c = tid; c < j; c += kConsumers) a.hvec[c] = dot[c];
+  if (tid == 0) {
+    st->x_norm = sqrt(dot[j]);
+    st->pending = 0;  // every CTA has read the flag and appended its rows of the column
+  }
+}
+
 template <typename S, int NC>
 __global__ void __launch_bounds__(kThreads, 2) lag_ws_kernel(const PassArgs a) {
   static_assert(sizeof(typename Compute<S>::T) == 4, "FP32/BF16 storage only");
@@ -286,58 +351,7 @@ __global__ void __launch_bounds__(kThreads, 2) lag_ws_kernel(const PassArgs a) {
     nrm[tid] = 0.0;
   }
 
-  // ---------------- cross-CTA reduction (as pass_epilogue), then h and ||x|| of the push
-  named_bar_sync(1, kConsumers);
-  if (tid == 0) {
-    double t = 0.0;
-    for (int i = 0; i < kConsumers; ++i) t += nrm[i];
-    dot[j] = t;
-  }
-  named_bar_sync(1, kConsumers);
-  const int len = j + 1;
-  double *mypart = a.partials + size_t(blockIdx.x) * (a.kmax + 1);
-  for (int c = tid; c < len; c += kConsumers) mypart[c] = dot[c];
-  __threadfence();
-  named_bar_sync(1, kConsumers);
-  const int ngroups = (gridDim.x + kGroup - 1) / kGroup;
-  const int grp = blockIdx.x / kGroup;
-  const int gfirst = grp * kGroup;
-  const int gsize = min(kGroup, int(gridDim.x) - gfirst);
-  if (tid == 0) {
-    const unsigned t = atomicAdd(&a.gcount[grp], 1u);
-    sflag[2] = (t == unsigned(gsize - 1)) ? 1 : 0;
-  }
-  named_bar_sync(1, kConsumers);
-  if (!sflag[2]) return;
-  __threadfence();
-  double *gp = a.gpart + size_t(grp) * (a.kmax + 1);
-  for (int c = tid; c < len; c += kConsumers) {
-    double t = 0.0;
-    for (int bq = 0; bq < gsize; ++bq) t += __ldcg(a.partials + size_t(gfirst + bq) * (a.kmax + 1) + c);
-    gp[c] = t;
-  }
-  __threadfence();
-  named_bar_sync(1, kConsumers);
-  if (tid == 0) {
-    a.gcount[grp] = 0u;
-    const unsigned t = atomicAdd(&st->ticket[PASS_A2], 1u);
-    sflag[2] = (t == unsigned(ngroups - 1)) ? 1 : 0;
-  }
-  named_bar_sync(1, kConsumers);
-  if (!sflag[2]) return;
-  __threadfence();
-  for (int c = tid; c < len; c += kConsumers) {
-    double t = 0.0;
-    for (int g = 0; g < ngroups; ++g) t += __ldcg(a.gpart + size_t(g) * (a.kmax + 1) + c);
-    dot[c] = t;
-  }
-  if (tid == 0) st->ticket[PASS_A2] = 0u;
-  named_bar_sync(1, kConsumers);
-  for (int c = tid; c < j; c += kConsumers) a.hvec[c] = dot[c];
-  if (tid == 0) {
-    st->x_norm = sqrt(dot[j]);
-    st->pending = 0;  // every CTA has read the flag and appended its rows of the column
-  }
+  lag_epilogue(a, st, dot, nrm, nullptr, sflag, j, jt, tid);
 }
 
 }  // namespace foa

@@ -225,7 +225,7 @@ def test_waves_2d_full_size(dt):
     print(dt, "kappa", kap, "errB", eB, "errH", eH)
 
 
-@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("bf16", 1), ("f32", 2)])
+@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("bf16", 1), ("f32", 2), ("bf16", 2)])
 def test_wide_basis_register_stage(dt, reorth):
     """N = 160 on a 96^2 waves grid (n = 9216): past j = 64 a pipeline stage is one or two 32-row
     tiles and the FP32/BF16 passes with column dots hold the stage in registers."""
@@ -236,3 +236,17 @@ def test_wide_basis_register_stage(dt, reorth):
     o, sts = run_oracle(Xr, 160, dt, tol=1e-12, reorth=reorth)
     assert len(infos) == len(sts) == 160
     compare_state(g, o, dt, 160)
+
+
+@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("f32", 2), ("bf16", 2)])
+def test_wide_basis_ragged(dt, reorth):
+    """n = 9001 (a ragged last tile, snapshot rows not 16-byte aligned, so x is read from global
+    memory instead of the staged slice), N = 140 Gaussian snapshots through the register-held
+    passes."""
+    n, N = 9001, 140
+    X = np.random.default_rng(9001).standard_normal((n, N))
+    Xr, Xd = to_device(X, dt)
+    g, infos = run_gpu(Xd, n, N, dt, reorth=reorth)
+    o, sts = run_oracle(Xr, N, dt, reorth=reorth)
+    assert [s[0] for s in infos] == [0] * N and all(s[0] == "ok" for s in sts)
+    compare_state(g, o, dt, N)
