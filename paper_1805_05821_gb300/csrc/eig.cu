@@ -87,10 +87,18 @@ __device__ __forceinline__ int block_max_int(int v, int *red) {
 // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2), s = c t,
 // a_i <- c a_i - s a_j,  a_j <- s a_i + c a_j.  Converged when no pair has
 // |gamma| > tol sqrt(alpha beta).  Afterwards sigma_i = |a_i| and u_i = a_i / sigma_i.
-__global__ void svd_jacobi_kernel(const double *B, int ldb, int m, double *A, int lda, double *sig, int *isc,
-                                  GridBar *gb, int max_sweeps, double tol) {
+//
+// A CTA of four warps (one per SM sub-partition, so the pair's FP64 work uses all four FP64
+// pipes of the SM) takes one column pair at a time: each thread holds up to kSvdRows rows of both
+// columns in registers, the three dot products are summed in a fixed order (warp trees, then the
+// four warps), thread 0 forms the rotation, and every thread rotates its rows.  The grid spans
+// the SMs (one pair per CTA per round of the round-robin ordering), one grid barrier per round.
+__global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B, int ldb, int m, double *A, int lda,
+                                                                 double *sig, int *isc, GridBar *gb, int max_sweeps,
+                                                                 double tol) {
   int *err = isc + ISC_ERR;
-  const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + tid;
   const int64_t gthreads = int64_t(gridDim.x) * blockDim.x;
   for (int64_t e = gtid; e < int64_t(m) * m; e += gthreads) {
     const int r = int(e % m), c = int(e / m);
@@ -98,60 +106,92 @@ __global__ void svd_jacobi_kernel(const double *B, int ldb, int m, double *A, in
   }
   if (gtid == 0) isc[ISC_ROT] = 0;
   if (!grid_barrier(gb, err)) return;
+  __shared__ double red[kSvdThreads / 32][3];
+  __shared__ double rcs[2];
+  __shared__ int rgo, nrot;
   const int mp = m + (m & 1);  // players of the round-robin schedule (m may be odd: one dummy)
   const int npairs = mp / 2;
-  const int warp_g = int(gtid >> 5);
-  const int nwarps = int(gthreads >> 5);
-  const int lane = threadIdx.x & 31;
+  const double tol2 = tol * tol;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    int myrot = 0;  // rotations applied by this CTA in the sweep (thread 0)
     for (int rnd = 0; rnd < mp - 1; ++rnd) {
-      for (int p = warp_g; p < npairs; p += nwarps) {
+      for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
         const int pa = p, pb = mp - 1 - p;
         const int i = pa == 0 ? 0 : 1 + (pa - 1 + rnd) % (mp - 1);
         const int j = pb == 0 ? 0 : 1 + (pb - 1 + rnd) % (mp - 1);
-        if (i >= m || j >= m) continue;
+        if (i >= m || j >= m) continue;  // uniform over the CTA
         double *ai = A + int64_t(i) * lda, *aj = A + int64_t(j) * lda;
+        double x[kSvdRows], y[kSvdRows];
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int k = lane; k < m; k += 32) {
-          const double x = ai[k], y = aj[k];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
+#pragma unroll
+        for (int u = 0; u < kSvdRows; ++u) {
+          const int k = tid + u * kSvdThreads;
+          x[u] = k < m ? ai[k] : 0.0;
+          y[u] = k < m ? aj[k] : 0.0;
+          al = fma(x[u], x[u], al);
+          be = fma(y[u], y[u], be);
+          ga = fma(x[u], y[u], ga);
         }
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (fabs(ga) > tol * sqrt(al * be) && ga != 0.0) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t);
-          const double s = c * t;
-          for (int k = lane; k < m; k += 32) {
-            const double x = ai[k], y = aj[k];
-            ai[k] = c * x - s * y;
-            aj[k] = s * x + c * y;
+        if (lane == 0) {
+          red[warp][0] = al;
+          red[warp][1] = be;
+          red[warp][2] = ga;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double sa = 0.0, sb = 0.0, sg = 0.0;
+          for (int w = 0; w < kSvdThreads / 32; ++w) {
+            sa += red[w][0];
+            sb += red[w][1];
+            sg += red[w][2];
           }
-          if (lane == 0) atomicAdd(&isc[ISC_ROT], 1);
+          const int go = (sg != 0.0) && (sg * sg > tol2 * (sa * sb));
+          if (go) {
+            const double zeta = (sb - sa) / (2.0 * sg);
+            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+            const double c = rsqrt(fma(t, t, 1.0));
+            rcs[0] = c;
+            rcs[1] = c * t;
+            ++myrot;
+          }
+          rgo = go;
+        }
+        __syncthreads();
+        if (rgo) {
+          const double c = rcs[0], sn = rcs[1];
+#pragma unroll
+          for (int u = 0; u < kSvdRows; ++u) {
+            const int k = tid + u * kSvdThreads;
+            if (k < m) {
+              ai[k] = c * x[u] - sn * y[u];
+              aj[k] = sn * x[u] + c * y[u];
+            }
+          }
         }
       }
       if (!grid_barrier(gb, err)) return;
     }
-    __shared__ int nrot;
-    if (threadIdx.x == 0) nrot = *(volatile int *)&isc[ISC_ROT];
+    if (tid == 0 && myrot) atomicAdd(&isc[ISC_ROT], myrot);
+    if (!grid_barrier(gb, err)) return;  // every CTA has added its count
+    if (tid == 0) nrot = *(volatile int *)&isc[ISC_ROT];
     if (!grid_barrier(gb, err)) return;  // everyone has read the count
     if (gtid == 0) isc[ISC_ROT] = 0;
     if (!grid_barrier(gb, err)) return;
     if (nrot == 0) break;
   }
   if (gtid == 0) isc[ISC_SWEEPS] = sweep;
-  // column norms
+  // column norms (one warp per column)
+  const int warp_g = int(gtid >> 5), nwarps = int(gthreads >> 5);
   for (int c = warp_g; c < m; c += nwarps) {
     const double *ac = A + int64_t(c) * lda;
-    double s = 0.0;
-    for (int k = lane; k < m; k += 32) s += ac[k] * ac[k];
-    s = warp_sum(s);
-    if (lane == 0) sig[c] = sqrt(s);
+    double sq = 0.0;
+    for (int k = lane; k < m; k += 32) sq += ac[k] * ac[k];
+    sq = warp_sum(sq);
+    if (lane == 0) sig[c] = sqrt(sq);
   }
 }
 
@@ -300,6 +340,7 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
   __shared__ int ired[32];
   __shared__ double sp, sq, sr, sx, sy, sz, st_, sw, sanorm;
   __shared__ int snn, sl, sm, sits, sskip, sfail;
+  __shared__ double fwd[3];  // column k, rows k+1..k+3, after step k of a sweep
   __syncthreads();
   double an = 0.0;
   for (int64_t e = threadIdx.x; e < int64_t(n) * n; e += blockDim.x) {
@@ -425,20 +466,23 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
       if (i != m + 2) AA(i, i - 3) = 0.0;
     }
     __syncthreads();
-    // double-shift QR sweep on rows/columns l..nn, starting at m
+    // double-shift QR sweep on rows/columns l..nn, starting at m.  The column update of step k
+    // produces column k's entries of rows k+1..k+3, which step k+1 reflects: the threads that
+    // compute them pass them on through shared memory (fwd) instead of a re-read.
     for (int k = m; k <= nn - 1; ++k) {
       if (threadIdx.x == 0) {
         double p = sp, q = sq, r = sr, x = 0.0;
         bool go = true;
         if (k != m) {
-          p = AA(k, k - 1);
-          q = AA(k + 1, k - 1);
-          r = (k != nn - 1) ? AA(k + 2, k - 1) : 0.0;
+          p = fwd[0];
+          q = fwd[1];
+          r = (k != nn - 1) ? fwd[2] : 0.0;
           x = fabs(p) + fabs(q) + fabs(r);
           if (x != 0.0) {
-            p /= x;
-            q /= x;
-            r /= x;
+            const double ix = 1.0 / x;
+            p *= ix;
+            q *= ix;
+            r *= ix;
           } else {
             go = false;
           }
@@ -455,11 +499,12 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
             AA(k, k - 1) = -s * x;
           }
           p += s;
-          sx = p / s;
-          sy = q / s;
-          sz = r / s;
-          sq = q / p;
-          sr = r / p;
+          const double is = 1.0 / s, ip = 1.0 / p;
+          sx = p * is;
+          sy = q * is;
+          sz = r * is;
+          sq = q * ip;
+          sr = r * ip;
           sskip = 0;
         } else {
           sskip = 1;
@@ -487,8 +532,13 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
             AA(i, k + 2) -= p * r;
           }
           AA(i, k + 1) -= p * q;
-          AA(i, k) -= p;
+          const double aik = AA(i, k) - p;
+          AA(i, k) = aik;
+          if (i > k) fwd[i - k - 1] = aik;
         }
+      } else {
+        // no reflection: the next step reads column k as it stands
+        for (int i = k + 1 + threadIdx.x; i <= k + 3 && i <= nn; i += blockDim.x) fwd[i - k - 1] = AA(i, k);
       }
       __syncthreads();
     }

@@ -87,16 +87,16 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
   else if (rank_tol < 0.0) tol = (m + 1) * eps_of(h->dtype);
   const bool trunc = tol > 0.0;
   if (trunc) {
-    // cooperative one-sided Jacobi SVD of beta_m (one warp per column pair)
-    int grid = ((m + 1) / 2 + 7) / 8;
-    if (grid > h->sms) grid = h->sms;
+    // cooperative one-sided Jacobi SVD of beta_m (one CTA of four warps per column pair and round)
+    int grid = (m + 1) / 2;
+    if (grid > 2 * h->sms) grid = 2 * h->sms;
     if (grid < 1) grid = 1;
     const double *Bp = h->B;
     int ldb = K, mm = m, lda = K, sweeps = 30, *iscp = w->isc;
     double *Ap = w->A, *sigp = w->sig_raw, jt = 4.0 * std::ldexp(1.0, -53) * std::sqrt(double(m));
     GridBar *gbp = w->gb;
     void *args[] = {&Bp, &ldb, &mm, &Ap, &lda, &sigp, &iscp, &gbp, &sweeps, &jt};
-    e = cudaLaunchCooperativeKernel((void *)svd_jacobi_kernel, grid, 256, args, 0, s);
+    e = cudaLaunchCooperativeKernel((void *)svd_jacobi_kernel, grid, kSvdThreads, args, 0, s);
     if (e != cudaSuccess) return cuda_status(e);
     svd_finish_kernel<<<1, 512, size_t(m) * 12 + 64, s>>>(w->A, K, m, w->sig_raw, w->U, w->sig, w->isc, tol);
     project_t_kernel<<<h->sms * 2, 256, 0, s>>>(h->H, K, m, w->U, K, w->isc, w->T, K);

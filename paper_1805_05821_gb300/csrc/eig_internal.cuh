@@ -54,6 +54,8 @@ struct EigWork {
   GridBar *gb = nullptr;
 };
 
+constexpr int kSvdThreads = 128;  // threads of a Jacobi SVD CTA (four warps per column pair)
+constexpr int kSvdRows = (kMaxK + kSvdThreads - 1) / kSvdThreads;
 __global__ void svd_jacobi_kernel(const double *B, int ldb, int m, double *A, int lda, double *sig, int *isc,
                                   GridBar *gb, int max_sweeps, double tol);
 __global__ void svd_finish_kernel(const double *A, int lda, int m, const double *sig_in, double *U, double *sig,
