@@ -53,6 +53,7 @@ static cudaError_t launch_lag_t(int mode, int nc, const PassArgs &a, int grid, c
     const int fc = fused_columns(a);
     if (fc == 16) return launch_lag_fused_one<S, 16>(a, grid, s);
     if (fc == 24) return launch_lag_fused_one<S, 24>(a, grid, s);
+    if (fc == 32) return launch_lag_fused_one<S, 32>(a, grid, s);
     switch (nc) {
       case 8: return launch_lag_ws_one<S, 8>(a, grid, s);
       case 16: return launch_lag_ws_one<S, 16>(a, grid, s);

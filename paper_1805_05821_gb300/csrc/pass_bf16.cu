@@ -51,6 +51,7 @@ static cudaError_t launch_ws(int nc, const PassArgs &a, int grid, cudaStream_t s
   const int fc = fused_columns(a);
   if (fc == 16) return launch_fused_one<MODE, 16>(a, grid, s);
   if (fc == 24) return launch_fused_one<MODE, 24>(a, grid, s);
+  if (fc == 32) return launch_fused_one<MODE, 32>(a, grid, s);
   switch (nc) {
     case 8: return launch_ws_one<MODE, 8>(a, grid, s);
     case 16: return launch_ws_one<MODE, 16>(a, grid, s);

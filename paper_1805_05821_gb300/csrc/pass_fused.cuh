@@ -25,7 +25,7 @@ inline int fused_columns(const PassArgs &a) {
   if (a.variant != 0 || a.R > 2) return 0;
   const int G1 = kConsumers / (a.R * (kTile / 2));
   const int cpg = (((a.jcap + G1 - 1) / G1) + 3) & ~3;
-  return cpg <= 16 ? 16 : cpg <= 24 ? 24 : 0;
+  return cpg <= 16 ? 16 : cpg <= 24 ? 24 : cpg <= 32 ? 32 : 0;
 }
 
 template <typename S, int MODE, int FC>

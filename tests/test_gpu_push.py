@@ -250,3 +250,16 @@ def test_wide_basis_ragged(dt, reorth):
     o, sts = run_oracle(Xr, N, dt, reorth=reorth)
     assert [s[0] for s in infos] == [0] * N and all(s[0] == "ok" for s in sts)
     compare_state(g, o, dt, N)
+
+
+@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("f32", 2), ("bf16", 1)])
+def test_widest_basis_register_stage(dt, reorth):
+    """k_max = 440 on n = 4097 Gaussian snapshots: past j = 384 a thread's column group holds up
+    to 32 columns (the widest register-held form)."""
+    n, N = 4097, 440
+    X = np.random.default_rng(4097).standard_normal((n, N))
+    Xr, Xd = to_device(X, dt)
+    g, infos = run_gpu(Xd, n, N, dt, reorth=reorth)
+    o, sts = run_oracle(Xr, N, dt, reorth=reorth)
+    assert [s[0] for s in infos] == [0] * N and all(s[0] == "ok" for s in sts)
+    compare_state(g, o, dt, N)
