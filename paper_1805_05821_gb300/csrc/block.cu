@@ -129,8 +129,15 @@ __device__ int chol_up(int p, const double *G, double *R) {
   return p;
 }
 
+// Two CTAs per SM while the column accumulators fit in 96 registers a thread (NQ * P <= 32, i.e.
+// j <= 256 for blocks of 4): one CTA's sweeps then overlap the other's.
+template <int NQ, int P>
+constexpr int block_min_blocks() {
+  return NQ * P <= 32 ? 2 : 1;
+}
+
 template <typename S, int MODE, int NQ, int P>
-__global__ void __launch_bounds__(kThreads, 1) block_kernel(const BlockArgs a) {
+__global__ void __launch_bounds__(kThreads, block_min_blocks<NQ, P>()) block_kernel(const BlockArgs a) {
   constexpr bool kRow = (MODE != BLK_A);   // row sweep (BLK_B, BLK_C)
   constexpr bool kCol = (MODE != BLK_C);   // column sweep (BLK_A, BLK_B)
   extern __shared__ __align__(128) unsigned char smem[];
@@ -686,8 +693,10 @@ cudaError_t launch_block_mode(int mode, int nq, const BlockArgs &a, int grid, cu
   }
 }
 
-// shared-memory layout and grid of a block pass at basis size j (one CTA per SM)
-bool block_geom(const foa_dmd *h, int P, int j, BlockArgs &a, int &grid) {
+// shared-memory layout and grid of a block pass at basis size j: two CTAs per SM when the kernel's
+// column accumulators allow it (block_min_blocks) and two ring slots fit in half the shared memory,
+// else one CTA per SM
+bool block_geom(const foa_dmd *h, int P, int j, bool two, BlockArgs &a, int &grid) {
   const int s = dtype_size(h->dtype);
   const int64_t tile_bytes = int64_t(kTile) * j * s;
   int R = 1;
@@ -698,7 +707,8 @@ bool block_geom(const foa_dmd *h, int P, int j, BlockArgs &a, int &grid) {
   const int64_t other = up(2 * int64_t(P) * R * kTile * 4, 128) + up(int64_t(j) * P * 4, 16) +
                         up(int64_t(j * P + P * P + P) * 8, 16) + int64_t(512) * P * 4 +
                         int64_t(kConsumers) * (P * (P + 1) / 2 > P ? P * (P + 1) / 2 : P) * 8 + 2 * kMaxSlots * 8 + 64;
-  int slots = int((int64_t(200) * 1024 - other) / slot);
+  if (two && 2 * slot + other > int64_t(112) * 1024) two = false;
+  int slots = int((int64_t(two ? 112 : 200) * 1024 - other) / slot);
   if (slots > 4) slots = 4;
   if (slots < 2) return false;
   a.R = R;
@@ -726,7 +736,8 @@ bool block_geom(const foa_dmd *h, int P, int j, BlockArgs &a, int &grid) {
   a.nrows = h->nrows;
   a.nstages = (h->ntiles + R - 1) / R;
   const int sms = h->sms - (h->opts.indicator_every > 0 ? 1 : 0);
-  grid = a.nstages < sms ? a.nstages : sms;
+  const int per_sm = two ? 2 : 1;
+  grid = a.nstages < sms * per_sm ? a.nstages : sms * per_sm;
   return true;
 }
 
@@ -742,7 +753,8 @@ int enqueue_block(foa_dmd *h, BlockWork &bw, const void *X, int64_t ldx, foa_dmd
   BlockArgs a;
   memset(&a, 0, sizeof(a));
   int grid = 0;
-  if (!block_geom(h, P, j, a, grid)) return FOA_DMD_EINVAL;
+  const int nq = nq_for(j);
+  if (!block_geom(h, P, j, nq * P <= 32, a, grid)) return FOA_DMD_EINVAL;
   a.V = h->V;
   a.X = X;
   a.ldx = ldx;
@@ -764,7 +776,6 @@ int enqueue_block(foa_dmd *h, BlockWork &bw, const void *X, int64_t ldx, foa_dmd
   cudaStream_t s = h->stream;
   block_prep_kernel<<<1, 32, 0, s>>>(h->st, bw.bs, j, P, h->kmax);
   cudaError_t e = cudaGetLastError();
-  const int nq = nq_for(j);
   const double sz = dtype_size(h->dtype), n = double(h->n);
   for (int mode = BLK_A; mode <= BLK_C && e == cudaSuccess; ++mode) {
     ProfScope ps(h, mode == BLK_A ? 0 : mode == BLK_B ? 1 : 2, n * j * sz + P * n * (mode == BLK_A ? sz : 8.0));
