@@ -66,6 +66,27 @@ __device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// Eight consecutive stage rows of one column (or one base slice), 32-byte aligned: two 16-byte
+// loads for FP32 (in the other order when swap, which keeps a wavefront's lanes on distinct
+// banks), one for BF16.
+__device__ __forceinline__ void ld8(const float *p, bool swap, float (&v)[8]) {
+  const float4 f = *reinterpret_cast<const float4 *>(p + (swap ? 4 : 0));
+  const float4 g = *reinterpret_cast<const float4 *>(p + (swap ? 0 : 4));
+  const float4 lo = swap ? g : f, hi = swap ? f : g;
+  v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+  v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+}
+__device__ __forceinline__ void ld8(const __nv_bfloat16 *p, bool, float (&v)[8]) {
+  const uint4 u = *reinterpret_cast<const uint4 *>(p);
+  const uint32_t q[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q[i]));
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
 // Cross-CTA reduction of len doubles (deterministic: CTA order within groups of 8, then group
 // order); returns true in the last CTA, with the sums in dot[0..len).
 __device__ bool block_reduce(const BlockArgs &a, double *dot, int len, int mode, volatile int *sflag, int tid) {
@@ -129,15 +150,12 @@ __device__ int chol_up(int p, const double *G, double *R) {
   return p;
 }
 
-// Two CTAs per SM while the column accumulators fit in 96 registers a thread (NQ * P <= 32, i.e.
-// j <= 256 for blocks of 4): one CTA's sweeps then overlap the other's.
-template <int NQ, int P>
-constexpr int block_min_blocks() {
-  return NQ * P <= 32 ? 2 : 1;
-}
-
-template <typename S, int MODE, int NQ, int P>
-__global__ void __launch_bounds__(kThreads, block_min_blocks<NQ, P>()) block_kernel(const BlockArgs a) {
+// Column sweep layout: thread t takes rows 8*(t%4) .. +7 of each tile and the columns
+// t/4 + 64*u, u < CT (CT = ceil(j/64) <= 8), so a thread keeps CT*P FP32 accumulators and the
+// P values of its eight rows, and every V element is read from shared memory once.  Two CTAs per
+// SM (96 registers a thread); one CTA's sweeps overlap the other's.
+template <typename S, int MODE, int CT, int P>
+__global__ void __launch_bounds__(kThreads, 2) block_kernel(const BlockArgs a) {
   constexpr bool kRow = (MODE != BLK_A);   // row sweep (BLK_B, BLK_C)
   constexpr bool kCol = (MODE != BLK_C);   // column sweep (BLK_A, BLK_B)
   extern __shared__ __align__(128) unsigned char smem[];
@@ -210,32 +228,45 @@ __global__ void __launch_bounds__(kThreads, block_min_blocks<NQ, P>()) block_ker
   }
 
   // ------------------------------------------------------------------ consumer warps
-  float acc[kCol ? NQ * P : 1];
+  float acc[kCol ? CT * P : 1];
 #pragma unroll
-  for (int q = 0; q < (kCol ? NQ * P : 1); ++q) acc[q] = 0.f;
-  float nrm[P];  // BLK_A: ||x_k||^2 of the rows this lane saw (quarter 0 of warp 0)
+  for (int q = 0; q < (kCol ? CT * P : 1); ++q) acc[q] = 0.f;
+  float nrm[P];  // BLK_A: ||x_k||^2 of the rows this thread saw (threads 0-3 cover every row)
 #pragma unroll
   for (int k = 0; k < P; ++k) nrm[k] = 0.f;
   double gram[NG];  // BLK_C: W^T W of the rows this thread finished
 #pragma unroll
   for (int q = 0; q < NG; ++q) gram[q] = 0.0;
-  const int l8 = lane & 7, qtr = lane >> 3;
+  const int rg = tid & 3, cg = tid >> 2;  // column sweep: row group (8 rows) and column group
+  // Fold the accumulators into the CTA's FP64 dot vector: the four threads of a column group
+  // (adjacent lanes) reduce-scatter their P partial sums, so that thread rg ends with p = rg and
+  // one FP64 add per column and warp suffices.
   auto flush = [&]() {
     if constexpr (kCol) {
 #pragma unroll
-      for (int kk = 0; kk < NQ; ++kk) {
-        const int c = warp + kWarps * (4 * kk + qtr);
-        if (warp + kWarps * (4 * kk) < j) {  // warp-uniform: the first quarter's column exists
-#pragma unroll
-          for (int k = 0; k < P; ++k) {
-            float v = (c < j) ? acc[kk * P + k] : 0.f;
-            v += __shfl_xor_sync(0xffffffffu, v, 4);
-            v += __shfl_xor_sync(0xffffffffu, v, 2);
-            v += __shfl_xor_sync(0xffffffffu, v, 1);
-            if (l8 == 0 && c < j) dot[c * P + k] += double(v);
-            acc[kk * P + k] = 0.f;
-          }
+      for (int u = 0; u < CT; ++u) {
+        const int c = cg + 64 * u;
+        float r;
+        if constexpr (P == 4) {
+          const bool hi = (rg & 2) != 0;
+          float x0 = hi ? acc[u * P + 2] : acc[u * P + 0], x1 = hi ? acc[u * P + 3] : acc[u * P + 1];
+          const float y0 = hi ? acc[u * P + 0] : acc[u * P + 2], y1 = hi ? acc[u * P + 1] : acc[u * P + 3];
+          x0 += __shfl_xor_sync(0xffffffffu, y0, 2);
+          x1 += __shfl_xor_sync(0xffffffffu, y1, 2);
+          const bool od = (rg & 1) != 0;
+          r = od ? x1 : x0;
+          r += __shfl_xor_sync(0xffffffffu, od ? x0 : x1, 1);
+        } else {
+          float x0 = acc[u * P + 0], x1 = acc[u * P + 1];
+          x0 += __shfl_xor_sync(0xffffffffu, x0, 2);
+          x1 += __shfl_xor_sync(0xffffffffu, x1, 2);
+          const bool od = (rg & 1) != 0;
+          r = od ? x1 : x0;
+          r += __shfl_xor_sync(0xffffffffu, od ? x0 : x1, 1);
         }
+        if (c < j && rg < P) dot[c * P + rg] += double(r);
+#pragma unroll
+        for (int k = 0; k < P; ++k) acc[u * P + k] = 0.f;
       }
     }
   };
@@ -335,38 +366,47 @@ __global__ void __launch_bounds__(kThreads, block_min_blocks<NQ, P>()) block_ker
 
     if constexpr (kCol) {
       // ---------------- column sweep: d_{c,k} = sum_r V_rc base_{r,k}
+      const bool swap = (cg & 1) != 0;  // odd column groups read their two row quads in the other order
       for (int kt = 0; kt < nt; ++kt) {
-        float4 wv[P];
+        const int row0 = kt * kTile + 8 * rg;
+        float w[8][P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
+          float t[8];
           if constexpr (MODE == BLK_B) {
-            wv[k] = *reinterpret_cast<const float4 *>(ws + k * (a.R * kTile) + kt * kTile + 4 * l8);
+            ld8(ws + k * (a.R * kTile) + row0, false, t);
+          } else if (bb) {
+            ld8(reinterpret_cast<const S *>(sbase + a.base_off + k * a.base_stride) + row0, false, t);
           } else {
-            const int row = kt * kTile + 4 * l8;
-            wv[k] = make_float4(base_at(k, row), base_at(k, row + 1), base_at(k, row + 2), base_at(k, row + 3));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t[i] = base_at(k, row0 + i);
           }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) w[i][k] = t[i];
         }
-        if (MODE == BLK_A && warp == 0 && qtr == 0) {
+        if (MODE == BLK_A && cg == 0) {
 #pragma unroll
           for (int k = 0; k < P; ++k)
-            nrm[k] += wv[k].x * wv[k].x + wv[k].y * wv[k].y + wv[k].z * wv[k].z + wv[k].w * wv[k].w;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) nrm[k] = fmaf(w[i][k], w[i][k], nrm[k]);
         }
-        const S *vt = vs + kt * (kTile * j) + 4 * l8;
+        const S *vt = vs + kt * (kTile * j) + 8 * rg;
 #pragma unroll
-        for (int kk = 0; kk < NQ; ++kk) {
-          const int c = warp + kWarps * (4 * kk + qtr);
+        for (int u = 0; u < CT; ++u) {
+          const int c = cg + 64 * u;
           if (c < j) {
-            const float4 v = ld4(vt + c * kTile);
+            float v[8];
+            ld8(vt + c * kTile, swap, v);
 #pragma unroll
-            for (int k = 0; k < P; ++k)
-              acc[kk * P + k] = fmaf(v.x, wv[k].x, fmaf(v.y, wv[k].y, fmaf(v.z, wv[k].z, fmaf(v.w, wv[k].w, acc[kk * P + k]))));
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+              for (int k = 0; k < P; ++k) acc[u * P + k] = fmaf(v[i], w[i][k], acc[u * P + k]);
           }
         }
-      }
-      since_flush += nt;
-      if (since_flush >= 8) {  // 32 products per lane and column
-        flush();
-        since_flush = 0;
+        if (++since_flush == 4) {  // 32 products per thread and column
+          flush();
+          since_flush = 0;
+        }
       }
     }
     __syncwarp();
@@ -660,9 +700,9 @@ struct BlockWork {
   foa_dmd_push_info *info = nullptr;
 };
 
-template <typename S, int MODE, int NQ, int P>
+template <typename S, int MODE, int CT, int P>
 cudaError_t launch_block_one(const BlockArgs &a, int grid, cudaStream_t s) {
-  auto k = block_kernel<S, MODE, NQ, P>;
+  auto k = block_kernel<S, MODE, CT, P>;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
@@ -674,28 +714,27 @@ cudaError_t launch_block_one(const BlockArgs &a, int grid, cudaStream_t s) {
 }
 
 template <typename S, int MODE, int P>
-cudaError_t launch_block_nq(int nq, const BlockArgs &a, int grid, cudaStream_t s) {
-  switch (nq) {
+cudaError_t launch_block_ct(int ct, const BlockArgs &a, int grid, cudaStream_t s) {
+  switch (ct) {
+    case 1: return launch_block_one<S, MODE, 1, P>(a, grid, s);
     case 2: return launch_block_one<S, MODE, 2, P>(a, grid, s);
     case 4: return launch_block_one<S, MODE, 4, P>(a, grid, s);
-    case 8: return launch_block_one<S, MODE, 8, P>(a, grid, s);
-    case 12: return launch_block_one<S, MODE, 12, P>(a, grid, s);
-    default: return launch_block_one<S, MODE, 16, P>(a, grid, s);
+    case 6: return launch_block_one<S, MODE, 6, P>(a, grid, s);
+    default: return launch_block_one<S, MODE, 8, P>(a, grid, s);
   }
 }
 
 template <typename S, int P>
-cudaError_t launch_block_mode(int mode, int nq, const BlockArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_block_mode(int mode, int ct, const BlockArgs &a, int grid, cudaStream_t s) {
   switch (mode) {
-    case BLK_A: return launch_block_nq<S, BLK_A, P>(nq, a, grid, s);
-    case BLK_B: return launch_block_nq<S, BLK_B, P>(nq, a, grid, s);
-    default: return launch_block_nq<S, BLK_C, P>(nq, a, grid, s);
+    case BLK_A: return launch_block_ct<S, BLK_A, P>(ct, a, grid, s);
+    case BLK_B: return launch_block_ct<S, BLK_B, P>(ct, a, grid, s);
+    default: return launch_block_ct<S, BLK_C, P>(ct, a, grid, s);
   }
 }
 
-// shared-memory layout and grid of a block pass at basis size j: two CTAs per SM when the kernel's
-// column accumulators allow it (block_min_blocks) and two ring slots fit in half the shared memory,
-// else one CTA per SM
+// shared-memory layout and grid of a block pass at basis size j: two CTAs per SM when two ring
+// slots fit in half the shared memory, else one CTA per SM
 bool block_geom(const foa_dmd *h, int P, int j, bool two, BlockArgs &a, int &grid) {
   const int s = dtype_size(h->dtype);
   const int64_t tile_bytes = int64_t(kTile) * j * s;
@@ -741,9 +780,10 @@ bool block_geom(const foa_dmd *h, int P, int j, bool two, BlockArgs &a, int &gri
   return true;
 }
 
-int nq_for(int j) {
-  const int need = (j + 31) / 32;
-  return need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : need <= 12 ? 12 : 16;
+// columns per thread of the column sweep (block_kernel's CT): ceil(j / 64), rounded up to an instance
+int ct_for(int j) {
+  const int need = (j + 63) / 64;
+  return need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : need <= 6 ? 6 : 8;
 }
 
 // one block of P snapshots (P = 2 or 4) on a stream with q >= 1 basis vectors
@@ -753,8 +793,8 @@ int enqueue_block(foa_dmd *h, BlockWork &bw, const void *X, int64_t ldx, foa_dmd
   BlockArgs a;
   memset(&a, 0, sizeof(a));
   int grid = 0;
-  const int nq = nq_for(j);
-  if (!block_geom(h, P, j, nq * P <= 32, a, grid)) return FOA_DMD_EINVAL;
+  const int ct = ct_for(j);
+  if (!block_geom(h, P, j, true, a, grid)) return FOA_DMD_EINVAL;
   a.V = h->V;
   a.X = X;
   a.ldx = ldx;
@@ -779,8 +819,8 @@ int enqueue_block(foa_dmd *h, BlockWork &bw, const void *X, int64_t ldx, foa_dmd
   const double sz = dtype_size(h->dtype), n = double(h->n);
   for (int mode = BLK_A; mode <= BLK_C && e == cudaSuccess; ++mode) {
     ProfScope ps(h, mode == BLK_A ? 0 : mode == BLK_B ? 1 : 2, n * j * sz + P * n * (mode == BLK_A ? sz : 8.0));
-    if (h->dtype == FOA_DMD_F32) e = launch_block_mode<float, P>(mode, nq, a, grid, s);
-    else e = launch_block_mode<__nv_bfloat16, P>(mode, nq, a, grid, s);
+    if (h->dtype == FOA_DMD_F32) e = launch_block_mode<float, P>(mode, ct, a, grid, s);
+    else e = launch_block_mode<__nv_bfloat16, P>(mode, ct, a, grid, s);
     h->launches += 1;
   }
   if (e == cudaSuccess) {

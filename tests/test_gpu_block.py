@@ -142,3 +142,23 @@ def test_block_push_wide_basis_fields():
     D = np.abs(lam[:, None] - spec.lam[None, :])
     ri, ci = linear_sum_assignment(D)
     assert np.max(D[ri, ci] / np.abs(spec.lam[ci])) <= 1e-5
+
+
+@pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4)])
+def test_block_push_widest_basis(dt, block):
+    """n = 4097 Gaussian snapshots (ragged last tile), N = 421 = 1 + 105 blocks of 4: the column
+    sweep's threads take up to eight columns each (j > 384) and every column-count instance runs."""
+    import torch
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    n, N = 4097, 421
+    X = np.random.default_rng(421).standard_normal((n, N))
+    Xr, Xd = to_device(X, dt)
+    ld = (n + 7) // 8 * 8
+    Xp = torch.zeros((N, ld), dtype=Xd.dtype, device="cuda")
+    Xp[:, :n] = Xd
+    g = FoaDMD(n, N, dt)
+    st, infos = g.push_block(Xp, block=block)
+    assert st == 0
+    o, sts = oracle_blocks(Xr, N, dt, block)
+    assert all(s[0] == "ok" for s in sts)
+    compare(g, o, dt, N)
