@@ -87,6 +87,23 @@ __device__ __forceinline__ void ld8(const __nv_bfloat16 *p, bool, float (&v)[8])
   }
 }
 
+// P consecutive floats (P = 2 or 4, 8- or 16-byte aligned) in one shared-memory access
+template <int P>
+__device__ __forceinline__ void ldp(const float *p, float (&v)[P]) {
+  if constexpr (P == 4) {
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  } else {
+    const float2 f = *reinterpret_cast<const float2 *>(p);
+    v[0] = f.x; v[1] = f.y;
+  }
+}
+template <int P>
+__device__ __forceinline__ void stp(float *p, const float (&v)[P]) {
+  if constexpr (P == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+
 // Cross-CTA reduction of len doubles (deterministic: CTA order within groups of 8, then group
 // order); returns true in the last CTA, with the sums in dot[0..len).
 __device__ bool block_reduce(const BlockArgs &a, double *dot, int len, int mode, volatile int *sflag, int tid) {
@@ -234,9 +251,12 @@ __global__ void __launch_bounds__(kThreads, 2) block_kernel(const BlockArgs a) {
   float nrm[P];  // BLK_A: ||x_k||^2 of the rows this thread saw (threads 0-3 cover every row)
 #pragma unroll
   for (int k = 0; k < P; ++k) nrm[k] = 0.f;
-  double gram[NG];  // BLK_C: W^T W of the rows this thread finished
+  double gram[NG];  // BLK_C: W^T W of the rows this thread finished (pair (k, l), l >= k, in order)
 #pragma unroll
   for (int q = 0; q < NG; ++q) gram[q] = 0.0;
+  double gslot[P];  // BLK_C, shared finish: products (k, k+i) of the rows' outputs k = tid % P
+#pragma unroll
+  for (int i = 0; i < P; ++i) gslot[i] = 0.0;
   const int rg = tid & 3, cg = tid >> 2;  // column sweep: row group (8 rows) and column group
   // Fold the accumulators into the CTA's FP64 dot vector: the four threads of a column group
   // (adjacent lanes) reduce-scatter their P partial sums, so that thread rg ends with p = rg and
@@ -328,9 +348,11 @@ __global__ void __launch_bounds__(kThreads, 2) block_kernel(const BlockArgs a) {
           float a0[P], a1[P];
 #pragma unroll
           for (int k = 0; k < P; ++k) a0[k] = a1[k] = 0.f;
+#pragma unroll 4
           for (int c = c0; c < c1; ++c) {
             const float2 v = ld_pair(vr + c * kTile);
-            const float *q = cf + c * P;
+            float q[P];
+            ldp<P>(cf + c * P, q);  // the P coefficients of column c (one 8- or 16-byte load)
 #pragma unroll
             for (int k = 0; k < P; ++k) {
               a0[k] = fmaf(v.x, q[k], a0[k]);
@@ -338,11 +360,8 @@ __global__ void __launch_bounds__(kThreads, 2) block_kernel(const BlockArgs a) {
             }
           }
           if (G1 > 1) {
-#pragma unroll
-            for (int k = 0; k < P; ++k) {
-              comb[(g * RS + row) * P + k] = a0[k];
-              comb[(g * RS + row + 1) * P + k] = a1[k];
-            }
+            stp<P>(comb + (g * RS + row) * P, a0);
+            stp<P>(comb + (g * RS + row + 1) * P, a1);
           } else {
             finish_row(row, a0);
             finish_row(row + 1, a1);
@@ -351,14 +370,26 @@ __global__ void __launch_bounds__(kThreads, 2) block_kernel(const BlockArgs a) {
       }
       if (G1 > 1) {
         named_bar_sync(1, kConsumers);
-        if (tid < RS) {
-          float s_[P];
+        // one (row, k) output per thread, the P outputs of a row on adjacent lanes; BLK_C's Gram
+        // products of the row are shared among those lanes (lane k takes the pairs (k, k+i))
+        for (int e0 = 0; e0 < RS * P; e0 += kConsumers) {
+          const int e = e0 + tid;
+          if (e < RS * P) {  // warp-uniform: RS * P is a multiple of 64
+            const int row = e / P, k = e % P;
+            float sum = 0.f;
+#pragma unroll 4
+            for (int g = 0; g < G1; ++g) sum += comb[(g * RS + row) * P + k];
+            const float wv = base_at(k, row) - sum;
+            a.W[int64_t(k) * a.nrows + (r0 + row)] = wv;
+            ws[k * (a.R * kTile) + row] = wv;
+            if constexpr (MODE == BLK_C) {
 #pragma unroll
-          for (int k = 0; k < P; ++k) s_[k] = 0.f;
-          for (int g = 0; g < G1; ++g)
-#pragma unroll
-            for (int k = 0; k < P; ++k) s_[k] += comb[(g * RS + tid) * P + k];
-          finish_row(tid, s_);
+              for (int i = 0; i < P; ++i) {
+                const float wl = __shfl_down_sync(0xffffffffu, wv, i);
+                if (k + i < P) gslot[i] += double(wv) * double(wl);  // exact products
+              }
+            }
+          }
         }
       }
       named_bar_sync(1, kConsumers);  // ws complete
@@ -424,6 +455,15 @@ __global__ void __launch_bounds__(kThreads, 2) block_kernel(const BlockArgs a) {
       dot[j * P + tid] = t;
     }
   } else if constexpr (MODE == BLK_C) {
+    {
+      const int kt = tid % P;  // the output index of this thread in the shared finish
+      int q = 0;
+#pragma unroll
+      for (int k = 0; k < P; ++k)
+#pragma unroll
+        for (int l = k; l < P; ++l, ++q)
+          if (k == kt) gram[q] += gslot[l - k];
+    }
 #pragma unroll
     for (int q = 0; q < NG; ++q) red[tid * NG + q] = gram[q];
     named_bar_sync(1, kConsumers);
