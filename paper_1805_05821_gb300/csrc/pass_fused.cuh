@@ -18,8 +18,8 @@
 
 namespace foa {
 
-// Columns per thread of the register-held pass for this launch (16 or 24), or 0 when the stage is
-// wider than two tiles, the column groups would exceed 24 columns, or the launch asks for the
+// Columns per thread of the register-held pass for this launch (16, 24 or 32), or 0 when the stage
+// is wider than two tiles, the column groups would exceed 32 columns, or the launch asks for the
 // shared-memory form (PassArgs::variant).
 inline int fused_columns(const PassArgs &a) {
   if (a.variant != 0 || a.R > 2) return 0;
