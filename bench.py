@@ -61,8 +61,11 @@ def parse():
     p.add_argument("--no-variants", action="store_true",
                    help="skip the secondary timing of the two-pass push on the same workload")
     p.add_argument("--sample-grid", type=int, default=40, help="grid of the CPU-oracle sample")
-    p.add_argument("--workload", default="fields", choices=["fields", "batched", "forms"],
-                   help="fields: the 4-field 256^3 stream (default); batched: 256 uneven planted streams")
+    p.add_argument("--workload", default="fields", choices=["fields", "batched", "forms", "waves3d"],
+                   help="fields: the 4-field 256^3 stream (default); batched: 256 uneven planted streams; "
+                        "forms: storage forms and the kappa sweep; waves3d: the 256^3 single-field waves "
+                        "(kappa_t 1e4) through the three-pass push and the block push of 4")
+    p.add_argument("--reps", type=int, default=2, help="waves3d: timed repetitions of each push form")
     p.add_argument("--streams", type=int, default=256)
     return p.parse_args()
 
@@ -242,6 +245,8 @@ def main():
         return run_batched(args)
     if args.workload == "forms":
         return run_forms(args)
+    if args.workload == "waves3d":
+        return run_waves3d(args)
     world, rank, local = dist_env()
     import torch
     if world > 1:
@@ -551,6 +556,83 @@ def run_batched(args):
                          "note": "V bytes of the three passes per push over the replay time"},
             "streams_ok": int(sum(1 for st in statuses if st == 0))}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_waves3d(args):
+    """Secondary measurement: the single-field waves on a G^3 grid (G = --grid, default 256, so
+    n = 16,777,216), N = --snapshots (500 when left at the fields default), kappa_t 1e4, FP32,
+    snapshots generated on the device.  Times the N pushes of the three-pass CGS2 push and of the
+    block push of 4 (foa_dmd_push_block: the first snapshot alone, then blocks of 4) with CUDA
+    events, --reps times each after one untimed run of each, and reports the per-pass-kind GB/s of
+    the handle's event counters."""
+    import ctypes
+    import torch
+    from paper_1805_05821_gb300 import build, synth
+    from paper_1805_05821_gb300 import foa_dmd as F
+    build.build()
+    G = args.grid
+    N = 500 if args.snapshots == 384 else args.snapshots
+    spec = synth.config3(0, kappa=1e4, G=G, N=N)
+    n = spec.n
+    X = torch.empty((N, n), dtype=torch.float32, device="cuda")
+    tabs = torch.from_numpy(np.stack(spec.tables).astype(np.float32)).cuda()
+    coefs = torch.from_numpy(np.ascontiguousarray(np.transpose(spec.T, (2, 0, 1))).astype(np.float32)).cuda()
+    for t in range(N):
+        F.foa_synth_waves(X[t], "f32", n, 3, G, 1, spec.M, tabs, coefs[t], spec.noise_scale, spec.seed_noise, t)
+    torch.cuda.synchronize()
+    L = F.lib()
+    opts = F.foa_dmd_opts_default()
+    opts.breakdown_tol = 1e-9
+    h = F.foa_dmd_create(n, N, "f32", opts)
+    if not args.no_tune:
+        F.foa_dmd_autotune(h)
+
+    def run(block):
+        F.foa_dmd_reset(h)
+        if block:
+            st = L.foa_dmd_push_block(h, ctypes.c_void_p(X.data_ptr()), N, n, block, None)
+        else:
+            st = 0
+            for t in range(N):
+                st = L.foa_dmd_push(h, ctypes.c_void_p(X[t].data_ptr()), None)
+                if st:
+                    break
+        if st:
+            raise RuntimeError(f"{'block' if block else 'three-pass'} push: {F.STATUS.get(st, st)}")
+
+    peak, _ = measured_peak()
+    out = {"metric": "snapshots/s of the N pushes (waves3d)", "unit": "snapshots/s", "data": "synthetic",
+           "dtype": "f32", "higher_is_better": True,
+           "config": {"workload": f"waves3d {G}^3 n={n} N={N} M={spec.M} kappa_t=1e4 FP32 (device-generated)",
+                      "timing": f"CUDA events over the N pushes, best of {args.reps} after one untimed run"}}
+    for label, block in (("three_pass", 0), ("block4", 4)):
+        run(block)  # untimed
+        best = None
+        for _ in range(args.reps):
+            F.foa_dmd_profile_read(h)
+            F.foa_dmd_profile(h, True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run(block)
+            e1.record()
+            torch.cuda.synchronize()
+            F.foa_dmd_profile(h, False)
+            stats = F.foa_dmd_profile_read(h)
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, stats)
+        ms, stats = best
+        kinds = {}
+        for k, name in enumerate(("A", "B", "C", "append/Q")):
+            if stats["ms"][k] > 0:
+                gbs = stats["bytes"][k] / (stats["ms"][k] / 1e3) / 1e9
+                kinds[name] = {"launches": stats["launches"][k], "GBps": gbs, "frac": gbs / peak}
+        out[label] = {"value": N / (ms / 1e3), "ms": ms, "q": F.foa_dmd_get_state(h, N)[0], "per_kind": kinds}
+    F.foa_dmd_destroy(h)
+    out["value"] = out["three_pass"]["value"]
+    print(json.dumps(out), flush=True)
     return 0
 
 
