@@ -46,8 +46,10 @@ static cudaError_t launch_fused_one(const PassArgs &a, int grid, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// passes with column dots (A, B, B2): the register-held kernel where its column groups fit,
+// else the warp-specialised one
 template <int MODE>
-static cudaError_t launch_ws(int nc, const PassArgs &a, int grid, cudaStream_t s) {
+static cudaError_t launch_dots(int nc, const PassArgs &a, int grid, cudaStream_t s) {
   const int fc = fused_columns(a);
   if (fc == 16) return launch_fused_one<MODE, 16>(a, grid, s);
   if (fc == 24) return launch_fused_one<MODE, 24>(a, grid, s);
@@ -61,22 +63,11 @@ static cudaError_t launch_ws(int nc, const PassArgs &a, int grid, cudaStream_t s
   }
 }
 
-template <int MODE>
-static cudaError_t launch_nc(int nc, const PassArgs &a, int grid, cudaStream_t s) {
-  switch (nc) {
-    case 8: return launch_one<MODE, 8>(a, grid, s);
-    case 16: return launch_one<MODE, 16>(a, grid, s);
-    case 32: return launch_one<MODE, 32>(a, grid, s);
-    case 48: return launch_one<MODE, 48>(a, grid, s);
-    default: return launch_one<MODE, 64>(a, grid, s);
-  }
-}
-
 cudaError_t launch_pass_f32(int mode, int nc, const PassArgs &a, int grid, cudaStream_t s) {
   switch (mode) {
-    case PASS_A: return launch_ws<PASS_A>(nc, a, grid, s);
-    case PASS_B: return launch_ws<PASS_B>(nc, a, grid, s);
-    case PASS_B2: return launch_ws<PASS_B2>(nc, a, grid, s);
+    case PASS_A: return launch_dots<PASS_A>(nc, a, grid, s);
+    case PASS_B: return launch_dots<PASS_B>(nc, a, grid, s);
+    case PASS_B2: return launch_dots<PASS_B2>(nc, a, grid, s);
     case PASS_C: return launch_one<PASS_C, 8>(a, grid, s);
     default: return launch_one<PASS_FIRST, 8>(a, grid, s);
   }
