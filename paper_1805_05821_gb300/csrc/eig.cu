@@ -339,7 +339,7 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
   __shared__ double red[32];
   __shared__ int ired[32];
   __shared__ double sp, sq, sr, sx, sy, sz, st_, sw, sanorm;
-  __shared__ int snn, sl, sm, sits, sskip, sfail;
+  __shared__ int snn, sits, sskip, sfail;
   __shared__ double fwd[3];  // column k, rows k+1..k+3, after step k of a sweep
   __syncthreads();
   double an = 0.0;
