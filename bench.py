@@ -24,6 +24,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -112,7 +113,9 @@ class ClockSampler:
     def __init__(self, gpu_uuid=None):
         self.proc = None
         self.uuid = gpu_uuid
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to FOA_DMD_CLOCKS_DIR (default: the system temporary directory)
+        d = os.environ.get("FOA_DMD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:

@@ -11,8 +11,8 @@ imports nothing from the product except the shared seeded input generators.
   the error indicators of Sec. 3.2.3 and the amplitudes of Sec. 3.2.4, Eqs. (exrecon)/(exreconwrt).
 * ``FoaOracle.modes`` forms the DMD modes V U_r z_i (Algorithm 1 step 26).
 
-Every function names the passage it follows.  Readings of the paper where it is silent or
-ambiguous are listed in the design doc and repeated in the docstrings here.
+Every function names the passage it follows; where the paper is silent or ambiguous, the docstring
+states the reading taken.
 """
 from __future__ import annotations
 
