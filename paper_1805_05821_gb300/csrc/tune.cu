@@ -183,7 +183,8 @@ extern "C" int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t fl
         g.inflight_bytes = c.inflight;
         g.max_ctas_per_sm = c.ctas;
         g.variant = c.variant;
-        // the register-held form exists for the FP32/BF16 passes with column dots only
+        // variant 1 (shared-memory stage instead of the register-held one) is an alternative for the
+        // FP32/BF16 passes with column dots only; FP64 and pass C have a single form
         if (c.variant == 1 && (h->dtype == FOA_DMD_F64 || mode == PASS_C)) continue;
         PassArgs a;
         memset(&a, 0, sizeof(a));
