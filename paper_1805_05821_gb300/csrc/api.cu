@@ -514,8 +514,10 @@ extern "C" int foa_dmd_get_basis(foa_dmd_t *h, int32_t col0, int32_t ncols, void
 
 extern "C" int foa_dmd_reset(foa_dmd_t *h) {
   if (!h) return FOA_DMD_EINVAL;
-  if (h->ind_stream) {
-    cudaError_t e0 = cudaStreamSynchronize(h->ind_stream);
+  if (h->ind_stream && h->ind_copied_set) {
+    // the side stream's eigensolve works on its own copies once it has read H-bar and beta: the
+    // reset's clearing waits for that read only, and the eigensolve may overlap the next pushes
+    cudaError_t e0 = cudaStreamWaitEvent(h->stream, h->ind_copied, 0);
     if (e0 != cudaSuccess) return cuda_status(e0);
   }
   h->pushes_host = 0;

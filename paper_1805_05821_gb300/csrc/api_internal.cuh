@@ -65,6 +65,8 @@ struct foa_dmd {
   foa::EigWork *ind_eig = nullptr;
   cudaStream_t ind_stream = nullptr;
   cudaEvent_t ind_event = nullptr;
+  cudaEvent_t ind_copied = nullptr;  // recorded once the latest indicator eigensolve has read H-bar/beta
+  bool ind_copied_set = false;
   void *ind_ring = nullptr;
   int64_t ind_issued = 0, ind_read = 0;
   bool ind_pending = false;

@@ -251,13 +251,21 @@ __global__ void project_g_kernel(const double *U, int ldu, int m, const int *isc
     G[i + int64_t(c) * ldg] = s;
   }
 }
-__global__ void copy_h_kernel(const double *H, int ldh, int m, double *G, int ldg, int *isc) {
+// G = H_m (Hessenberg part), and the two entries of the stream's state the untruncated eigen path
+// still needs (h_{m+1,m} for the indicators, beta_11 for the amplitudes), so that nothing after this
+// kernel reads H-bar or beta.
+__global__ void copy_h_kernel(const double *H, int ldh, int m, double *G, int ldg, int *isc, const double *B,
+                              double *scal) {
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < int64_t(m) * m;
        e += int64_t(gridDim.x) * blockDim.x) {
     const int i = int(e % m), c = int(e / m);
     G[i + int64_t(c) * ldg] = (i <= c + 1) ? H[i + int64_t(c) * ldh] : 0.0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) isc[ISC_R] = m;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    isc[ISC_R] = m;
+    scal[0] = H[m + int64_t(m - 1) * ldh];
+    scal[1] = B[0];
+  }
 }
 
 // ------------------------------------------------------------------------------ Hessenberg

@@ -14,7 +14,7 @@ static constexpr int kVecGridMax = 64;  // CTAs of the inverse-iteration kernel 
 static void free_work(EigWork *w) {
   void *ptrs[] = {w->A,  w->U,  w->sig_raw, w->sig, w->G,      w->Q,     w->T,     w->Aqr,   w->wr,
                   w->wi, w->yr, w->yi,      w->ysr, w->ysi,    w->ind,   w->amp_re, w->amp_im, w->out,
-                  w->anorm, w->lu, w->tw, w->yplanes, w->perm, w->isc, w->gb, w->bop};
+                  w->anorm, w->lu, w->tw, w->yplanes, w->perm, w->isc, w->gb, w->bop, w->scal};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;
@@ -29,6 +29,9 @@ void eig_free(foa_dmd *h) {
   h->ind_ring = nullptr;
   if (h->ind_event) cudaEventDestroy(h->ind_event);
   h->ind_event = nullptr;
+  if (h->ind_copied) cudaEventDestroy(h->ind_copied);
+  h->ind_copied = nullptr;
+  h->ind_copied_set = false;
   if (h->ind_stream) cudaStreamDestroy(h->ind_stream);
   h->ind_stream = nullptr;
 }
@@ -53,6 +56,7 @@ static int eig_alloc(foa_dmd *h, EigWork **slot) {
   AL(w->lu, size_t(w->vgrid) * 2 * K2); AL(w->tw, size_t(w->vgrid) * 2 * K1); AL(w->yplanes, 2 * K2);
   AL(w->perm, size_t(K) * 4); AL(w->isc, ISC_N * 4); AL(w->gb, sizeof(GridBar));
   AL(w->bop, modes_tc_bop_bytes(K));
+  AL(w->scal, 2 * 8);
 #undef AL
   if (e == cudaSuccess) e = cudaMemset(w->gb, 0, sizeof(GridBar));
   if (e == cudaSuccess) e = cudaMemset(w->isc, 0, ISC_N * 4);
@@ -78,7 +82,10 @@ struct EigOut {
 // Enqueue the eigen path on stream s with workspace w for the projected matrix of size m: all
 // launch sizes are bounded by m and the truncated rank r is read on the device, so nothing here
 // waits for the GPU.  rank_tol as for foa_dmd_eig.
-static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double rank_tol, int nsel) {
+// copied (nullable) is recorded on s once the enqueued work has read the stream's state (H-bar,
+// beta): right after copy_h_kernel on the untruncated path, at the end on the truncated one.
+static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double rank_tol, int nsel,
+                       cudaEvent_t copied = nullptr) {
   const int K = h->kmax;
   cudaError_t e = cudaMemsetAsync(w->isc, 0, ISC_N * 4, s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -104,7 +111,11 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
     hessenberg_kernel<<<1, 512, size_t(m) * 8 + 32 * 8, s>>>(w->G, K, w->Q, K, w->isc);
     h->launches += 5;
   } else {
-    copy_h_kernel<<<h->sms, 256, 0, s>>>(h->H, K, m, w->G, K, w->isc);
+    copy_h_kernel<<<h->sms, 256, 0, s>>>(h->H, K, m, w->G, K, w->isc, h->B, w->scal);
+    if (copied) {
+      e = cudaEventRecord(copied, s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
     h->launches += 1;
   }
   anorm_kernel<<<1, 512, 0, s>>>(w->G, K, w->isc, w->anorm);
@@ -143,14 +154,18 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
   a.m = m;
   a.have_q = trunc ? 1 : 0;
   a.have_u = trunc ? 1 : 0;
-  a.hlast_p = h->H + m + int64_t(m - 1) * K;  // h_{m+1,m} (0 after a breakdown)
-  a.b11_p = h->B;
+  a.hlast_p = trunc ? h->H + m + int64_t(m - 1) * K : w->scal;  // h_{m+1,m} (0 after a breakdown)
+  a.b11_p = trunc ? h->B : w->scal + 1;
   const int vgrid = m < w->vgrid ? m : w->vgrid;
   const size_t vsmem = (size_t(m) * 10 + size_t(m + 1) / 2 + 64) * 8;
   vectors_kernel<<<vgrid, 256, vsmem, s>>>(a);
   if (nsel > m) nsel = m;
   order_kernel<<<1, 512, size_t(m) * 20 + 64, s>>>(a, nsel);
   h->launches += 4;  // anorm, hqr, vectors, order
+  if (trunc && copied) {
+    e = cudaEventRecord(copied, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   return cuda_status(cudaGetLastError());
 }
 
@@ -226,6 +241,7 @@ int maybe_indicator(foa_dmd *h) {
     e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->ind_stream, cudaStreamNonBlocking, lo);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ind_event, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ind_copied, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&h->ind_ring, sizeof(IndRecord) * kIndRing);
     if (e != cudaSuccess) return cuda_status(e);
   }
@@ -234,8 +250,9 @@ int maybe_indicator(foa_dmd *h) {
   e = cudaEventRecord(h->ind_event, h->stream);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(h->ind_stream, h->ind_event, 0);
   if (e != cudaSuccess) return cuda_status(e);
-  rc = enqueue_eig(h, h->ind_eig, h->ind_stream, m, h->opts.indicator_rank_tol, 0);
+  rc = enqueue_eig(h, h->ind_eig, h->ind_stream, m, h->opts.indicator_rank_tol, 0, h->ind_copied);
   if (rc) return rc;
+  h->ind_copied_set = true;
   IndRecord *rec = static_cast<IndRecord *>(h->ind_ring) + (h->ind_issued % kIndRing);
   ind_record_kernel<<<1, 32, 0, h->ind_stream>>>(h->ind_eig->out, h->kmax, h->ind_eig->isc, h->opts.n_lead, rec,
                                                  h->pushes_host, m);

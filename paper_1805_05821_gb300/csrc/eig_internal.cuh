@@ -50,6 +50,7 @@ struct EigWork {
          *ind = nullptr, *amp_re = nullptr, *amp_im = nullptr, *out = nullptr, *anorm = nullptr, *lu = nullptr,
          *tw = nullptr, *yplanes = nullptr;
   float *bop = nullptr;  // pre-split Y operand of the tensor-core mode product
+  double *scal = nullptr;  // untruncated path: h_{m+1,m} and beta_11, copied with H_m
   int *perm = nullptr, *isc = nullptr;
   GridBar *gb = nullptr;
 };
@@ -64,7 +65,8 @@ __global__ void project_t_kernel(const double *H, int ldh, int m, const double *
                                  double *T, int ldt);
 __global__ void project_g_kernel(const double *U, int ldu, int m, const int *isc, const double *T, int ldt, double *G,
                                  int ldg);
-__global__ void copy_h_kernel(const double *H, int ldh, int m, double *G, int ldg, int *isc);
+__global__ void copy_h_kernel(const double *H, int ldh, int m, double *G, int ldg, int *isc, const double *B,
+                              double *scal);
 __global__ void hessenberg_kernel(double *G, int ldg, double *Q, int ldq, const int *isc);
 __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, double *wi, int *isc, int use_smem);
 __global__ void vectors_kernel(EigArgs e);

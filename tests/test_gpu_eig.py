@@ -145,6 +145,32 @@ def test_indicator_schedule():
             assert np.isnan(inf["indicator"])
 
 
+def test_reset_while_an_indicator_runs():
+    """A reset right after a push that scheduled an indicator eigensolve: the reset waits only until
+    the side stream has copied H-bar and beta, and neither run disturbs the other.  The second
+    run's state equals a fresh handle's bit for bit, and the indicators of both runs agree."""
+    spec = synth.config2(4, G=48, N=10)
+    X = synth.snapshots(spec)
+    Xr, Xd = to_device(X, "f64")
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    g = FoaDMD(spec.n, 10, "f64", indicator_every=5, n_lead=4)
+    for rep in range(2):
+        g.reset()
+        for t in range(10):
+            assert g.push(Xd[t], info=False)[0] == 0
+    q, stopped, H, B = g.state()
+    f = FoaDMD(spec.n, 10, "f64", indicator_every=5, n_lead=4)
+    for t in range(10):
+        assert f.push(Xd[t], info=False)[0] == 0
+    qf, _, Hf, Bf = f.state()
+    assert q == qf == 10 and np.array_equal(H, Hf) and np.array_equal(B, Bf)
+    rec = g.indicators()
+    assert [(r[0], r[1]) for r in rec] == [(5, 4), (10, 9), (5, 4), (10, 9)], rec
+    assert rec[0][2] == rec[2][2] and rec[1][2] == rec[3][2], rec
+    recf = f.indicators()
+    assert [r[2] for r in recf] == [rec[0][2], rec[1][2]]
+
+
 def test_tensor_core_modes_match_simt_and_oracle(monkeypatch):
     """Phi = V Y on tcgen05 (three-term TF32 split) against the SIMT FP32 kernel and the oracle,
     with a ragged n (not a multiple of the 256-row block) and m not a multiple of 16."""
