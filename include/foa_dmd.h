@@ -49,7 +49,9 @@ typedef enum {
                               the stream freezes and the j x j projected matrix is exact */
   FOA_DMD_ESTOPPED = 6,    /* push after a breakdown */
   FOA_DMD_ENONFINITE = 7,  /* snapshot holds NaN or Inf; state unchanged */
-  FOA_DMD_ETIMEOUT = 8,    /* a bounded device wait ran out; the handle should be destroyed */
+  FOA_DMD_ETIMEOUT = 8,    /* a bounded device wait ran out and the waiting kernel returned;
+                              from foa_dmd_eig the stream state is unchanged and the handle
+                              stays usable, after a push call the handle should be destroyed */
   FOA_DMD_EIO = 9,         /* checkpoint file error or checksum mismatch */
   FOA_DMD_ENOCONV = 10     /* the device eigensolver did not converge */
 } foa_dmd_status;
@@ -192,6 +194,17 @@ typedef struct {
 int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *res);
 
 /*
+ * Test hook for the failure path of the bounded device waits (no counterpart in the paper).
+ * The next truncated foa_dmd_eig of this handle launches its cooperative SVD with CTA skip_cta
+ * (clamped to the grid) returning before its first grid-barrier arrival, as a CTA that died
+ * would, and every other CTA giving up after spin_cycles clock cycles (1 .. 2^32; the normal
+ * limit is 2^32, about 2 s at 2 GHz).  That eig returns FOA_DMD_ETIMEOUT with the stream state
+ * unchanged; the barrier is re-armed at every launch, so the next eig runs normally.  One shot:
+ * the request is cleared by the launch it affects.  Errors: EINVAL.
+ */
+int foa_dmd_test_wait_fault(foa_dmd_t *h, int32_t skip_cta, int64_t spin_cycles);
+
+/*
  * Copy the FP64 state to host buffers (synchronises): q, stopped flag, H-bar and beta as
  * k_max x k_max column-major arrays with leading dimension ld >= k_max (either may be NULL).
  */
@@ -220,15 +233,15 @@ int foa_dmd_load(const char *path, const foa_dmd_opts *opts, foa_dmd_t **out);
 
 /*
  * One push that allocates no device memory, for callers that cannot call cudaMalloc at that
- * point (an arena or pool owns all device memory, a host application forbids allocation on its
- * hot path, or the work is issued into a region captured for replay).  The paper has no
- * counterpart: it is the arithmetic of foa_dmd_push (Alg. 4 with p = 1) on buffers the caller
- * owns, with the library's per-push scratch in a fixed file-scope device array instead of
- * allocated memory.
+ * point (an arena or pool owns all device memory, or a host application forbids allocation on
+ * its hot path).  The paper has no counterpart: it is the arithmetic of foa_dmd_push (Alg. 4
+ * with p = 1) on buffers the caller owns, with the library's per-push scratch in a fixed
+ * file-scope device array instead of allocated memory.
  *   V:        device, row-tiled basis as described at foa_dmd_get_basis (n rounded up to a
  *             multiple of 32 rows, k_max columns per tile, storage dtype, zero-initialised);
  *   Hbar, beta: device, k_max x k_max FP64 column-major (zero-initialised before the first push);
- *   q:        current number of basis vectors (0 for the first snapshot);
+ *   q:        current number of basis vectors (0 for the first snapshot; after an OK push the
+ *             new q is info->q, after EBREAKDOWN q stays as it was);
  *   x_dev:    device, the snapshot (n elements, storage dtype, 16-byte aligned);
  *   w_dev:    device, working vector of ceil(n/32)*32 elements (FP32, or FP64 for FP64 storage),
  *             zero-initialised once; on return it holds the unnormalised new direction;
@@ -238,7 +251,12 @@ int foa_dmd_load(const char *path, const foa_dmd_opts *opts, foa_dmd_t **out);
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
  * should therefore come before any stream capture.  Every call shares the array and clears
  * what must start at zero; calls that overlap on the GPU (different streams or threads) race
- * on it.  The call synchronises cuda_stream before returning.  Errors as for foa_dmd_push.
+ * on it.  The call synchronises cuda_stream before returning.  There is no handle to remember
+ * a breakdown: the caller's H-bar is the record.  A breakdown (EBREAKDOWN) writes h into H-bar
+ * column q (1-based) and leaves q alone; a later call with that q finds the column non-zero and
+ * returns ESTOPPED without changing anything (a zero first snapshot records nothing, so a call
+ * after it starts the stream afresh).  Errors: EINVAL (sizes beyond the limits, null pointers),
+ * EFULL, EBREAKDOWN, ESTOPPED, ENONFINITE, ETIMEOUT, ECUDA.
  */
 int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, void *V, double *Hbar, double *beta,
                          int32_t q, const void *x_dev, void *w_dev, double breakdown_tol, void *cuda_stream,

@@ -71,6 +71,9 @@ struct foa_dmd {
   int64_t ind_issued = 0, ind_read = 0;
   bool ind_pending = false;
   bool ind_this_push = false;  // the most recent push scheduled an indicator
+  // foa_dmd_test_wait_fault: one-shot failure injection into the next cooperative SVD launch
+  int test_skip_cta = -1;
+  long long test_spin_cycles = 0;
 };
 
 namespace foa {

@@ -2,11 +2,12 @@
 //
 //   svd_jacobi_kernel  one-sided (Hestenes) Jacobi SVD of the upper-triangular beta_m, run by a
 //                      cooperative grid: each round of the round-robin ordering rotates m/2
-//                      independent column pairs, one pair per warp; beta_m W = U Sigma gives
-//                      U and Sigma without forming W (Sec. 3.2.2 rank truncation).
-//   project_kernel     G = U_r^T H_m U_r (or G = H_m without truncation).
+//                      independent column pairs, one pair per CTA of four warps; beta_m W =
+//                      U Sigma gives U and Sigma without forming W (Sec. 3.2.2 rank truncation).
+//   project_t/g_kernel G = U_r^T H_m U_r (copy_h_kernel: G = H_m without truncation).
 //   hessenberg_kernel  Householder reduction of G to upper Hessenberg form G = Q Hs Q^T.
-//   hqr_kernel         eigenvalues of Hs by the Francis double-shift QR iteration (single CTA).
+//   hqr_kernel         eigenvalues of Hs by the Francis double-shift QR iteration (single CTA;
+//                      the sequential steps of the EISPACK routine hqr).
 //   vectors_kernel     per eigenvalue: right and left eigenvectors of Hs by inverse iteration
 //                      (LU of Hs - lambda I with adjacent-row pivoting), z = Q z_hs normalised
 //                      (unit norm, largest entry real positive), the amplitude
@@ -25,8 +26,10 @@
 namespace foa {
 
 // ------------------------------------------------------------------------------ grid barrier
-// Only used in cooperative launches (all CTAs co-resident).  Bounded spin.
-__device__ bool grid_barrier(GridBar *gb, int *err) {
+// Only used in cooperative launches (all CTAs co-resident).  Bounded spin: a CTA that has waited
+// spin_limit clock cycles for the others records FOA_DMD_ETIMEOUT and returns false, and its
+// caller returns at once, so a CTA that never arrives ends the whole grid within the limit.
+__device__ bool grid_barrier(GridBar *gb, int *err, long long spin_limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -42,7 +45,7 @@ __device__ bool grid_barrier(GridBar *gb, int *err) {
     } else {
       const long long t0 = clock64();
       while (*vgen == gen) {
-        if (clock64() - t0 > (1ll << 32)) {
+        if (clock64() - t0 > spin_limit) {
           ok = 0;
           atomicExch(err, FOA_DMD_ETIMEOUT);
           break;
@@ -93,9 +96,13 @@ __device__ __forceinline__ int block_max_int(int v, int *red) {
 // columns in registers, the three dot products are summed in a fixed order (warp trees, then the
 // four warps), thread 0 forms the rotation, and every thread rotates its rows.  The grid spans
 // the SMs (one pair per CTA per round of the round-robin ordering), one grid barrier per round.
+//
+// skip_cta (normally -1) and spin_limit serve foa_dmd_test_wait_fault: CTA skip_cta returns before
+// its first grid-barrier arrival, as a CTA that died would, and the others give up after
+// spin_limit cycles.
 __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B, int ldb, int m, double *A, int lda,
                                                                  double *sig, int *isc, GridBar *gb, int max_sweeps,
-                                                                 double tol) {
+                                                                 double tol, long long spin_limit, int skip_cta) {
   int *err = isc + ISC_ERR;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + tid;
@@ -105,7 +112,8 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B
     A[r + int64_t(c) * lda] = (r <= c) ? B[r + int64_t(c) * ldb] : 0.0;
   }
   if (gtid == 0) isc[ISC_ROT] = 0;
-  if (!grid_barrier(gb, err)) return;
+  if (int(blockIdx.x) == skip_cta) return;  // failure injection only (uniform over the CTA)
+  if (!grid_barrier(gb, err, spin_limit)) return;
   __shared__ double red[kSvdThreads / 32][3];
   __shared__ double rcs[2];
   __shared__ int rgo, nrot;
@@ -173,14 +181,14 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B
           }
         }
       }
-      if (!grid_barrier(gb, err)) return;
+      if (!grid_barrier(gb, err, spin_limit)) return;
     }
     if (tid == 0 && myrot) atomicAdd(&isc[ISC_ROT], myrot);
-    if (!grid_barrier(gb, err)) return;  // every CTA has added its count
+    if (!grid_barrier(gb, err, spin_limit)) return;  // every CTA has added its count
     if (tid == 0) nrot = *(volatile int *)&isc[ISC_ROT];
-    if (!grid_barrier(gb, err)) return;  // everyone has read the count
+    if (!grid_barrier(gb, err, spin_limit)) return;  // everyone has read the count
     if (gtid == 0) isc[ISC_ROT] = 0;
-    if (!grid_barrier(gb, err)) return;
+    if (!grid_barrier(gb, err, spin_limit)) return;
     if (nrot == 0) break;
   }
   if (gtid == 0) isc[ISC_SWEEPS] = sweep;
@@ -328,14 +336,23 @@ __global__ void hessenberg_kernel(double *G, int ldg, double *Q, int ldq, const 
 
 // ------------------------------------------------------------------------------ QR iteration
 // Eigenvalues of the upper Hessenberg Hs (n x n) by the Francis double-shift QR iteration with
-// deflation (Golub & Van Loan, Sec. 7.5; exceptional shifts after 10 and 20 iterations without
-// deflation).  Works in place on a copy A.  A conjugate pair is stored +Im first.
-__global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, double *wi, int *isc, int use_smem) {
+// deflation.  The sequential core follows the published routine hqr of Martin, Peters and
+// Wilkinson ("The QR algorithm for real Hessenberg matrices", Numer. Math. 14 (1970) 219-231;
+// Handbook for Automatic Computation vol. II, contribution II/14; EISPACK hqr): the negligible-
+// subdiagonal search, the exceptional shifts after 10 and 20 iterations without deflation
+// (0.75 s and -0.4375 s^2), the search for two small consecutive subdiagonals and the bulge-
+// chasing sweep with its p, q, r, x, y, z, w quantities (Golub & Van Loan, Sec. 7.5, give the
+// same method).  Here the row and column updates of every sweep step are spread over the CTA.
+// Works in place on a copy A.  A conjugate pair is stored +Im first.
+__global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, double *wi, int *isc,
+                           int smem_elems) {
   const int n = isc_in[ISC_R];
   extern __shared__ double sh[];
   double *a = Ag;
   int ld = lda;
-  if (use_smem) {
+  // The order n is known only here (the truncated rank r is counted on the device): the matrix is
+  // copied into the dynamic shared memory whenever it fits the smem_elems doubles provided.
+  if (int64_t(n) * n <= int64_t(smem_elems)) {
     a = sh;
     ld = n;
     for (int64_t e = threadIdx.x; e < int64_t(n) * n; e += blockDim.x) {

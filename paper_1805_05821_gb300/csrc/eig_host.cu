@@ -1,4 +1,5 @@
 // Host orchestration of the device eigen path: foa_dmd_eig and the push-time indicator schedule.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -10,6 +11,7 @@
 namespace foa {
 
 static constexpr int kVecGridMax = 64;  // CTAs of the inverse-iteration kernel (each owns LU scratch)
+static constexpr int kQrSmemMaxOrder = 160;  // largest order whose matrix (200 KB) the QR iteration keeps in shared memory
 
 static void free_work(EigWork *w) {
   void *ptrs[] = {w->A,  w->U,  w->sig_raw, w->sig, w->G,      w->Q,     w->T,     w->Aqr,   w->wr,
@@ -102,7 +104,17 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
     int ldb = K, mm = m, lda = K, sweeps = 30, *iscp = w->isc;
     double *Ap = w->A, *sigp = w->sig_raw, jt = 4.0 * std::ldexp(1.0, -53) * std::sqrt(double(m));
     GridBar *gbp = w->gb;
-    void *args[] = {&Bp, &ldb, &mm, &Ap, &lda, &sigp, &iscp, &gbp, &sweeps, &jt};
+    long long spin = kGridSpinCycles;
+    int skip = -1;
+    if (h->test_skip_cta >= 0) {  // foa_dmd_test_wait_fault (one shot)
+      skip = h->test_skip_cta < grid ? h->test_skip_cta : grid - 1;
+      spin = h->test_spin_cycles;
+      h->test_skip_cta = -1;
+    }
+    // a barrier that timed out keeps a partial count: every launch starts from a zeroed one
+    e = cudaMemsetAsync(w->gb, 0, sizeof(GridBar), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    void *args[] = {&Bp, &ldb, &mm, &Ap, &lda, &sigp, &iscp, &gbp, &sweeps, &jt, &spin, &skip};
     e = cudaLaunchCooperativeKernel((void *)svd_jacobi_kernel, grid, kSvdThreads, args, 0, s);
     if (e != cudaSuccess) return cuda_status(e);
     svd_finish_kernel<<<1, 512, size_t(m) * 12 + 64, s>>>(w->A, K, m, w->sig_raw, w->U, w->sig, w->isc, tol);
@@ -121,13 +133,15 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
   anorm_kernel<<<1, 512, 0, s>>>(w->G, K, w->isc, w->anorm);
   e = cudaMemcpyAsync(w->Aqr, w->G, size_t(K) * K * 8, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  const size_t qr_smem = size_t(m) * m * 8;
-  const bool use_smem = qr_smem <= 200 * 1024;
-  if (use_smem && qr_smem > 48 * 1024) {
+  // The QR iteration works on the r x r matrix (r = m without truncation); r is counted on the
+  // device, so the launch offers min(m^2, 160^2) doubles of shared memory and the kernel copies the
+  // matrix there when r^2 fits (every truncated eig with r <= 160, whatever m).
+  const size_t qr_smem = std::min(size_t(m) * m, size_t(kQrSmemMaxOrder) * kQrSmemMaxOrder) * 8;
+  if (qr_smem > 48 * 1024) {
     e = cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
     if (e != cudaSuccess) return cuda_status(e);
   }
-  hqr_kernel<<<1, 512, use_smem ? qr_smem : 0, s>>>(w->Aqr, K, w->isc, w->wr, w->wi, w->isc, use_smem ? 1 : 0);
+  hqr_kernel<<<1, 512, qr_smem, s>>>(w->Aqr, K, w->isc, w->wr, w->wi, w->isc, int(qr_smem / 8));
   EigArgs a;
   memset(&a, 0, sizeof(a));
   a.Hs = w->G;
@@ -278,6 +292,13 @@ double latest_indicator(foa_dmd *h, bool only_if_pending) {
 }  // namespace foa
 
 using namespace foa;
+
+extern "C" int foa_dmd_test_wait_fault(foa_dmd_t *h, int32_t skip_cta, int64_t spin_cycles) {
+  if (!h || skip_cta < 0 || spin_cycles < 1 || spin_cycles > kGridSpinCycles) return FOA_DMD_EINVAL;
+  h->test_skip_cta = skip_cta;
+  h->test_spin_cycles = spin_cycles;
+  return FOA_DMD_OK;
+}
 
 extern "C" int foa_dmd_eig(foa_dmd_t *h, double rank_tol, foa_dmd_eig_result *res) {
   if (!h || !res) return FOA_DMD_EINVAL;

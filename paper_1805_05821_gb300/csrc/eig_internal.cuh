@@ -57,8 +57,9 @@ struct EigWork {
 
 constexpr int kSvdThreads = 128;  // threads of a Jacobi SVD CTA (four warps per column pair)
 constexpr int kSvdRows = (kMaxK + kSvdThreads - 1) / kSvdThreads;
+constexpr long long kGridSpinCycles = 1ll << 32;  // bounded wait of a grid barrier (about 2 s at 2 GHz)
 __global__ void svd_jacobi_kernel(const double *B, int ldb, int m, double *A, int lda, double *sig, int *isc,
-                                  GridBar *gb, int max_sweeps, double tol);
+                                  GridBar *gb, int max_sweeps, double tol, long long spin_limit, int skip_cta);
 __global__ void svd_finish_kernel(const double *A, int lda, int m, const double *sig_in, double *U, double *sig,
                                   int *isc, double rank_tol);
 __global__ void project_t_kernel(const double *H, int ldh, int m, const double *U, int ldu, const int *isc,
@@ -68,7 +69,8 @@ __global__ void project_g_kernel(const double *U, int ldu, int m, const int *isc
 __global__ void copy_h_kernel(const double *H, int ldh, int m, double *G, int ldg, int *isc, const double *B,
                               double *scal);
 __global__ void hessenberg_kernel(double *G, int ldg, double *Q, int ldq, const int *isc);
-__global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, double *wi, int *isc, int use_smem);
+__global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, double *wi, int *isc,
+                           int smem_elems);
 __global__ void vectors_kernel(EigArgs e);
 __global__ void order_kernel(EigArgs e, int nsel);
 __global__ void anorm_kernel(const double *Hs, int ld, const int *isc, double *out);

@@ -1,13 +1,13 @@
 // One push without any device allocation: foa_dmd_push_noalloc.
 //
 // Some callers cannot allocate device memory at the point where they need the update: code
-// running under a memory pool or arena that owns all device memory, plug-ins whose host
-// application forbids cudaMalloc/cudaFree on its hot path (they may synchronise the device or
-// fragment a carefully sized heap), or code replayed inside a captured CUDA graph region that was
-// set up before.  For them this entry point performs the same push as foa_dmd_push on buffers the
-// caller already owns; the library's own per-push scratch (device state, beta_pre/h/s vectors,
-// the per-CTA partial sums of the cross-CTA reduction and their counters) lives in one
-// file-scope __device__ array of fixed size instead of memory obtained with cudaMalloc.
+// running under a memory pool or arena that owns all device memory, or plug-ins whose host
+// application forbids cudaMalloc/cudaFree on its hot path (those calls may synchronise the
+// device or fragment a carefully sized heap).  For them this entry point performs the same push
+// as foa_dmd_push on buffers the caller already owns; the library's own per-push scratch (device
+// state, beta_pre/h/s vectors, the per-CTA partial sums of the cross-CTA reduction and their
+// counters) lives in one file-scope __device__ array of fixed size instead of memory obtained
+// with cudaMalloc.  The call waits for its stream to finish the push before it returns.
 #include <cstring>
 
 #include "api_internal.cuh"
@@ -31,8 +31,13 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 // Device address of g_scratch per device, looked up once per device.
 static void *g_addr[64];
 
-__global__ void init_state_kernel(DevState *st, int q, int stopped) {
+// The caller's buffers are the whole stream state.  A breakdown leaves q unchanged and records
+// h in H-bar column q (1-based), a column that is still zero on a stream that has not broken
+// down; such a stream is marked stopped, so the push reports FOA_DMD_ESTOPPED as a handle would.
+__global__ void init_state_kernel(DevState *st, int q, const double *Hbar, int ldh) {
   if (threadIdx.x == 0) {
+    int stopped = 0;
+    for (int i = 0; i < q && q > 0; ++i) stopped |= Hbar[i + int64_t(q - 1) * ldh] != 0.0;
     st->q = q;
     st->stopped = stopped;
   }
@@ -98,18 +103,18 @@ extern "C" int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, voi
   cudaError_t e = cudaMemsetAsync(st, 0, kStateBytes, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(gcount, 0, kCountBytes, s);
   if (e != cudaSuccess) return cuda_status(e);
-  foa::na::init_state_kernel<<<1, 32, 0, s>>>(st, q, 0);
+  foa::na::init_state_kernel<<<1, 32, 0, s>>>(st, q, Hbar, k_max);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_status(e);
   rc = enqueue_push(&h, x_dev, false, nullptr);
+  h.V = h.w = nullptr;  // the stand-in owns nothing
   if (rc) return rc;
-  e = cudaMemcpyAsync(info, &st->info, sizeof(*info), cudaMemcpyDeviceToHost, s);
+  // one copy brings back the push result together with the sticky device error word
+  DevState out;
+  e = cudaMemcpyAsync(&out, st, sizeof(out), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
-  int32_t err = 0;
-  e = cudaMemcpy(&err, &st->err, sizeof(err), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_status(e);
-  if (err) return err;
-  h.V = h.w = nullptr;  // the stand-in owns nothing
+  *info = out.info;
+  if (out.err) return out.err;
   return info->status < 0 ? FOA_DMD_ECUDA : info->status;
 }

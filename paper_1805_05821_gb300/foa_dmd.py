@@ -75,6 +75,7 @@ def lib():
             "foa_dmd_indicators": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), _DP, i32,
                                                   ctypes.POINTER(i32)]),
             "foa_dmd_eig": (ctypes.c_int, [vp, d, ctypes.POINTER(foa_dmd_eig_result)]),
+            "foa_dmd_test_wait_fault": (ctypes.c_int, [vp, i32, i64]),
             "foa_dmd_get_state": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), _DP, _DP, i32]),
             "foa_dmd_get_basis": (ctypes.c_int, [vp, i32, i32, vp, i64]),
             "foa_dmd_reset": (ctypes.c_int, [vp]),
@@ -228,6 +229,10 @@ def foa_dmd_eig(h, rank_tol, cap, n_modes=0, phi=None, ld_phi=0, vec_cols=0, wan
             m = res.m
             out["vec"] = (vr[:m * vc].reshape(vc, m).T + 1j * vi[:m * vc].reshape(vc, m).T)
     return out
+
+
+def foa_dmd_test_wait_fault(h, skip_cta, spin_cycles):
+    return lib().foa_dmd_test_wait_fault(h, int(skip_cta), int(spin_cycles))
 
 
 def foa_dmd_push_noalloc(n, k_max, dtype, V, Hbar, beta, q, x, w, breakdown_tol=0.0, stream=None):
@@ -419,6 +424,9 @@ class FoaDMD:
 
     def reset(self):
         foa_dmd_reset(self.h)
+
+    def test_wait_fault(self, skip_cta, spin_cycles):
+        return foa_dmd_test_wait_fault(self.h, skip_cta, spin_cycles)
 
     def save(self, path):
         return foa_dmd_save(self.h, path)

@@ -1,15 +1,17 @@
 """Batched streams (one persistent launch per push of every stream) against the FP64 oracle.
 
 Streams of uneven n and k_max, FP32 storage, planted maps with noise (the batched workload's
-recipe at small sizes); some streams sit out some pushes.  Each stream's beta and H-bar must
-match an oracle run on the same rounded inputs within k_max u_fp32 kappa_2(X).
+recipe at small sizes, with 1e-3 instead of 1e-5 relative noise so that u_fp32 kappa_2(X) stays
+below 1e-2); some streams sit out some pushes.  Each stream's beta and H-bar must match an
+oracle run on the same rounded inputs column by column within C u_fp32 kappa_2(X_{1:p})
+(gpu_util).
 """
 import ctypes
 
 import numpy as np
 import pytest
 
-from gpu_util import U, kappa_of, rel, to_device
+from gpu_util import PARITY_C, PARITY_MAX_BOUND, U, compare_columns, kappa_of, rel, to_device
 from paper_1805_05821_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -27,7 +29,7 @@ def make_streams():
     for s in range(6):
         n = int(rng.integers(500, 70000))
         N = int(rng.integers(10, 40))
-        out.append(synth.planted(n, N, int(rng.integers(6, 12)) * 2, seed=100 + s, noise_rel=1e-5))
+        out.append(synth.planted(n, N, int(rng.integers(6, 12)) * 2, seed=100 + s, noise_rel=1e-3))
     return out
 
 
@@ -93,11 +95,7 @@ def test_batched_streams_match_oracle(use_graph):
             q, status, H, B = F.foa_dmd_batch_get_state(b, s, sp.N)
             o = oracle_state(hosts[s], sp.N)
             assert q == o.q, (s, q, o.q)
-            kap = kappa_of(o.B, q)
-            tol = sp.N * U["f32"] * kap
-            assert rel(B[:q, :q], o.B[:q, :q]) <= tol, s
-            m = o.m
-            assert rel(H[:m + 1, :m], o.H[:m + 1, :m]) <= tol, s
+            compare_columns(q, o.m, H, B, o, "f32", label=f"stream {s} n={sp.n}")
     finally:
         F.foa_dmd_batch_destroy(b)
 
@@ -108,7 +106,7 @@ def test_batched_equals_single_stream_structure():
     import torch
     from paper_1805_05821_gb300 import foa_dmd as F
     from paper_1805_05821_gb300.foa_dmd import FoaDMD
-    sp = synth.planted(40000, 30, 16, seed=5, noise_rel=1e-5)
+    sp = synth.planted(40000, 30, 16, seed=5, noise_rel=1e-3)
     Xr, Xd = to_device(synth.snapshots(sp), "f32")
     g = FoaDMD(sp.n, 30, "f32", breakdown_tol=1e-9)
     for t in range(30):
@@ -125,6 +123,7 @@ def test_batched_equals_single_stream_structure():
     q2, st, H2, B2 = F.foa_dmd_batch_get_state(b, 0, 30)
     F.foa_dmd_batch_destroy(b)
     assert q1 == q2 == 30
-    # two FP32 summation orders: agreement to k_max u_fp32 kappa_2(X), like the oracle comparisons
-    tol = 30 * U["f32"] * kappa_of(B1, 30)
+    # two FP32 summation orders: agreement to C u_fp32 kappa_2(X), like the oracle comparisons
+    tol = PARITY_C * U["f32"] * kappa_of(B1, 30)
+    assert tol <= PARITY_MAX_BOUND
     assert rel(B2, B1) <= tol and rel(H2[:30, :29], H1[:30, :29]) <= tol

@@ -1,14 +1,16 @@
 """GPU parity of the streaming push (Alg. 1 steps 2-18, Alg. 4) against the FP64 oracle.
 
 Every case runs the CUDA path through the C ABI and the oracle on the same (storage-rounded)
-inputs.  Tolerances: FP64 storage 1e-10 normwise on beta and H-bar; FP32/BF16 storage
-k_max * u_storage * kappa_2(X) normwise (the error law of Eq. foabaseddmdberr with the
-N-type factors of App. B taken as k_max), kappa_2 measured from the oracle's beta.
+inputs.  Tolerances: FP64 storage 1e-10 normwise on beta and H-bar; FP32/BF16 storage column by
+column, ||delta col|| / ||col|| <= C u_s kappa_2(X_{1:p}) with the fixed C of gpu_util (the error
+law of Sec. 3.2.2, Eq. foabaseddmdberr), and only on inputs where that bound is at most 1e-2.
+Ill-conditioned reduced-precision sequences are compared through their leading eigenvalues.
 """
 import numpy as np
 import pytest
 
-from gpu_util import U, kappa_of, rel, run_gpu, run_oracle, to_device
+from gpu_util import (U, compare_eigs, compare_state, gaussian, kappa_of, rel, run_gpu, run_oracle,
+                      to_device)
 from paper_1805_05821_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -20,21 +22,6 @@ def built():
     build.build()
 
 
-def compare_state(g, o, dt, k_max, q_expect=None, tol=None):
-    q, stopped, H, B = g.state()
-    assert q == o.q and stopped == o.stopped
-    if q_expect is not None:
-        assert q == q_expect
-    m = o.m
-    kap = kappa_of(o.B, q)
-    if tol is None:
-        tol = 1e-10 if dt == "f64" else k_max * U[dt] * kap
-    eB = rel(B[:q, :q], o.B[:q, :q])
-    eH = rel(H[:m + 1, :m], o.H[:m + 1, :m]) if m >= 1 else 0.0
-    assert eB <= tol, (eB, tol)
-    assert eH <= tol, (eH, tol)
-    return eB, eH, kap
-
 
 def test_planted_rank10_fp64_breakdown():
     """n=4096, N=32 planted rank-10 map: breakdown at push 11 on both sides, state within 1e-10."""
@@ -45,7 +32,7 @@ def test_planted_rank10_fp64_breakdown():
     o, sts = run_oracle(Xr, 32, "f64")
     assert len(infos) == 11 and infos[-1][0] == 5  # FOA_DMD_EBREAKDOWN at push 11
     assert sts[-1][0] == "breakdown" and len(sts) == 11
-    compare_state(g, o, "f64", 32, q_expect=10)
+    compare_state(g, o, "f64", q_expect=10)
     Vg = g.basis(0, 10).double().cpu().numpy().T
     assert rel(Vg, o.V[:, :10]) <= 1e-10
     for (st, inf), so in zip(infos[:-1], sts[:-1]):
@@ -62,20 +49,24 @@ def test_ragged_fp64(n):
     g, infos = run_gpu(Xd, n, N, "f64")
     o, sts = run_oracle(Xr, N, "f64")
     assert [s[0] for s in infos] == [0 if s[0] == "ok" else 5 for s in sts]
-    compare_state(g, o, "f64", N)
+    compare_state(g, o, "f64")
 
 
 @pytest.mark.parametrize("dt", ["f32", "bf16"])
 def test_precision_forms(dt):
-    """FP32/BF16 storage, FP32 products, FP64 blocked accumulation (waves on a 96^2 grid)."""
-    spec = synth.config2(2, G=96, N=40)
-    X = synth.snapshots(spec)
+    """FP32/BF16 storage, FP32 products, FP64 blocked accumulation.  FP32: 40 undamped waves on a
+    96^2 grid with 1e-3 noise (kappa_2 = 33); BF16: Gaussian snapshots of the same shape
+    (kappa_2 = 1.14), since u_bf16 kappa must stay below 1e-2."""
+    if dt == "f32":
+        X = synth.snapshots(synth.waves(96, 2, 1, 40, 40, 2, sigma=None, noise_rel=1e-3))
+    else:
+        X = gaussian(9216, 40, 2)
+    n = X.shape[0]
     Xr, Xd = to_device(X, dt)
-    g, infos = run_gpu(Xd, spec.n, 40, dt)
+    g, infos = run_gpu(Xd, n, 40, dt)
     o, sts = run_oracle(Xr, 40, dt)
-    assert len(infos) == len(sts)
-    eB, eH, kap = compare_state(g, o, dt, 40)
-    print(dt, "kappa", kap, "errB", eB, "errH", eH)
+    assert len(infos) == len(sts) == 40
+    compare_state(g, o, dt, with_basis=True, label="precision forms")
 
 
 @pytest.mark.parametrize("dt", ["f64", "f32", "bf16"])
@@ -157,7 +148,7 @@ def test_cgs1_option():
     Xr, Xd = to_device(X, "f64")
     g, _ = run_gpu(Xd, spec.n, 20, "f64", reorth=0)
     o, _ = run_oracle(Xr, 20, "f64", reorth=0)
-    compare_state(g, o, "f64", 20)
+    compare_state(g, o, "f64")
 
 
 def test_checkpoint_resume_is_bitwise(tmp_path):
@@ -214,31 +205,44 @@ def test_device_generator_matches_host_rows():
 
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_waves_2d_full_size(dt):
-    """1024 x 1024 grid (n = 2^20), N = 200, 20 damped waves, noise 1e-6 relative."""
+    """1024 x 1024 grid (n = 2^20), N = 200, 20 damped waves, noise 1e-6 relative (kappa_2 = 1.8e6).
+    FP64: state within 1e-10.  FP32: u_s kappa_2(X) is far above 1e-2, so the state is not
+    comparable column by column; the truncated eig (automatic rank) is, through the 20 leading
+    eigenvalues (compare_eigs)."""
     spec = synth.config2(0)
     X = synth.snapshots(spec)
     Xr, Xd = to_device(X, dt)
     g, infos = run_gpu(Xd, spec.n, 200, dt)
     o, sts = run_oracle(Xr, 200, dt)
     assert len(infos) == len(sts)
-    eB, eH, kap = compare_state(g, o, dt, 200)
-    print(dt, "kappa", kap, "errB", eB, "errH", eH)
+    if dt == "f64":
+        compare_state(g, o, dt)
+        return
+    import oracle as orc
+    rg = g.eig(rank_tol=-1.0)
+    ro = o.eig(orc.auto_rank_tol(dt, o.m + 1))
+    assert rg["status"] == 0
+    compare_eigs(rg, ro, dt, 20, label="waves 1024^2")
 
 
 @pytest.mark.parametrize("dt,reorth", [("f32", 1), ("bf16", 1), ("f32", 2), ("bf16", 2)])
 def test_wide_basis_register_stage(dt, reorth):
-    """N = 160 on a 96^2 waves grid (n = 9216): past j = 64 a pipeline stage is one or two 32-row
-    tiles and the FP32/BF16 passes with column dots hold the stage in registers."""
-    spec = synth.config2(6, G=96, N=160)
-    X = synth.snapshots(spec)
+    """N = 160 on n = 9216 rows: past j = 64 a pipeline stage is one or two 32-row tiles and the
+    FP32/BF16 passes with column dots hold the stage in registers.  FP32: 100 undamped waves on a
+    96^2 grid with 1e-2 noise (kappa_2 = 210); BF16: Gaussian snapshots (kappa_2 = 1.3)."""
+    if dt == "f32":
+        X = synth.snapshots(synth.waves(96, 2, 1, 160, 100, 6, sigma=None, noise_rel=1e-2))
+    else:
+        X = gaussian(9216, 160, 6)
+    n = X.shape[0]
     Xr, Xd = to_device(X, dt)
-    g, infos = run_gpu(Xd, spec.n, 160, dt, reorth=reorth, breakdown_tol=1e-12)
+    g, infos = run_gpu(Xd, n, 160, dt, reorth=reorth, breakdown_tol=1e-12)
     o, sts = run_oracle(Xr, 160, dt, tol=1e-12, reorth=reorth)
     assert len(infos) == len(sts) == 160
-    compare_state(g, o, dt, 160)
+    compare_state(g, o, dt, with_basis=True, label=f"register stage reorth={reorth}")
 
 
-@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("f32", 2), ("bf16", 2)])
+@pytest.mark.parametrize("dt,reorth", [("f32", 1), ("f32", 2), ("bf16", 1), ("bf16", 2)])
 def test_wide_basis_ragged(dt, reorth):
     """n = 9001 (a ragged last tile, snapshot rows not 16-byte aligned, so x is read from global
     memory instead of the staged slice), N = 140 Gaussian snapshots through the register-held
@@ -249,7 +253,7 @@ def test_wide_basis_ragged(dt, reorth):
     g, infos = run_gpu(Xd, n, N, dt, reorth=reorth)
     o, sts = run_oracle(Xr, N, dt, reorth=reorth)
     assert [s[0] for s in infos] == [0] * N and all(s[0] == "ok" for s in sts)
-    compare_state(g, o, dt, N)
+    compare_state(g, o, dt, with_basis=True, label=f"ragged n=9001 reorth={reorth}")
 
 
 @pytest.mark.parametrize("dt,reorth", [("f32", 1), ("f32", 2), ("bf16", 1)])
@@ -262,4 +266,4 @@ def test_widest_basis_register_stage(dt, reorth):
     g, infos = run_gpu(Xd, n, N, dt, reorth=reorth)
     o, sts = run_oracle(Xr, N, dt, reorth=reorth)
     assert [s[0] for s in infos] == [0] * N and all(s[0] == "ok" for s in sts)
-    compare_state(g, o, dt, N)
+    compare_state(g, o, dt, with_basis=True, label=f"widest n=4097 reorth={reorth}")
