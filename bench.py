@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="skip the launch-geometry autotuner (untimed setup)")
     p.add_argument("--no-variants", action="store_true",
-                   help="skip the secondary timing of the two-pass push on the same workload")
+                   help="skip the secondary lines: the two-pass push on the same workload and the FP64/FP32/BF16 "
+                        "storage forms on the 1024^2 waves")
     p.add_argument("--sample-grid", type=int, default=40, help="grid of the CPU-oracle sample")
     p.add_argument("--workload", default="fields", choices=["fields", "batched", "forms", "waves3d"],
                    help="fields: the 4-field 256^3 stream (default); batched: 256 uneven planted streams; "
@@ -382,6 +383,10 @@ def main():
         phi = None
         torch.cuda.empty_cache()
         out["variants"] = {"two_pass": run_variant(args, spec, X, n, N, F, L, world, 2)}
+    # ---- the storage forms on the 1024^2 waves (rank 0 of a one-rank run)
+    if not args.no_variants and rank == 0 and world == 1:
+        torch.cuda.empty_cache()
+        out.setdefault("variants", {})["forms"] = run_forms_variant(F, torch)
     # ---- CPU oracle baseline (rank 0) and the FP32-vs-FP64 eigenvalue error on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(args.sample_grid, N, args.indicator_every, nm, n, args.reorth)
@@ -479,6 +484,72 @@ def run_variant(args, spec, X, n, N, F, L, world, reorth, block=0):
                 "leading32_rel_err_vs_planted": float(np.max(D[ri, ci] / np.abs(spec.lam[ci])))}
     finally:
         F.foa_dmd_destroy(h)
+
+
+def run_forms_variant(F, torch, reps=2):
+    """Secondary line for the precision forms: the same snapshots (the 1024^2 waves, n = 2^20,
+    N = 200, 20 damped waves, noise 1e-6, kappa_2 about 1.8e6) stored in FP64, FP32 and BF16.
+    Per form: snapshots/s of the N pushes alone and of the pushes plus the untruncated eig
+    (CUDA events, one warm-up run and `reps` timed runs), and the relative error of the 20 leading
+    eigenvalues (the oracle's |c| order, matched one to one) against ONE FP64 oracle run on the
+    unrounded FP64 snapshots, so the storage rounding of the inputs counts in each form's error;
+    the error against the planted eigenvalues e^{sigma +- i omega} is given beside it."""
+    import oracle
+    from paper_1805_05821_gb300 import synth
+    spec = synth.config2(0)
+    n, N = spec.n, spec.N
+    X = torch.empty((N, n), dtype=torch.float64, device="cuda")
+    tabs = torch.from_numpy(np.stack(spec.tables).astype(np.float64)).cuda()
+    for t in range(N):
+        coef = torch.from_numpy(np.ascontiguousarray(spec.T[:, :, t]).astype(np.float64)).cuda()
+        F.foa_synth_waves(X[t], "f64", n, 2, spec.grid[0], 1, spec.M, tabs, coef, spec.noise_scale,
+                          spec.seed_noise, t)
+    torch.cuda.synchronize()
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+    forms = {}
+    for dt in ("f64", "f32", "bf16"):
+        Xc = X.to(tdt[dt]).contiguous()
+        g = F.FoaDMD(n, N, dt, breakdown_tol=BREAKDOWN_TOL)
+        t_push, t_all = [], []
+        for rep in range(reps + 1):
+            g.reset()
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            for t in range(N):
+                st, _ = g.push(Xc[t], info=False)
+                if st != 0:
+                    raise RuntimeError(f"forms {dt} push {t}: {F.STATUS.get(st, st)}")
+            e1.record()
+            res = g.eig(0.0)
+            e2.record()
+            torch.cuda.synchronize()
+            if rep:
+                t_push.append(e0.elapsed_time(e1) / 1e3)
+                t_all.append(e0.elapsed_time(e2) / 1e3)
+        g.close()
+        del Xc
+        forms[dt] = {"pushes_per_s": N / statistics.median(t_push), "snapshots_per_s_with_eig": N / statistics.median(t_all),
+                     "lam": res["lam"], "status": res["status"]}
+    Xh = X.cpu().numpy().T
+    del X
+    o = oracle.FoaOracle(n, N, breakdown_tol=BREAKDOWN_TOL, storage="f64")
+    for t in range(N):
+        if o.push(np.ascontiguousarray(Xh[:, t]))[0] != "ok":
+            break
+    ro = o.eig(0.0)
+    lead = ro["lam"][:20]
+    sv = np.linalg.svd(o.B[:o.q, :o.q], compute_uv=False)
+    out = {"workload": f"waves2d 1024^2 n={n} N={N} (20 damped waves, noise 1e-6), kappa_2(X) = {sv[0] / sv[-1]:.3g}",
+           "eig": "untruncated (rank_tol 0)", "reps": reps,
+           "error": "max relative error of the 20 leading eigenvalues against the FP64 oracle on the FP64 snapshots"}
+    for dt, f in forms.items():
+        out[dt] = {"pushes_per_s": f["pushes_per_s"], "snapshots_per_s_with_eig": f["snapshots_per_s_with_eig"],
+                   "leading20_eig_rel_err_vs_fp64_oracle": _match_rel(lead, f["lam"]),
+                   "leading20_eig_rel_err_vs_planted": _match_rel(f["lam"][:20], spec.lam)}
+    out["f32_over_f64_snapshots_per_s"] = out["f32"]["snapshots_per_s_with_eig"] / out["f64"]["snapshots_per_s_with_eig"]
+    out["bf16_over_f64_snapshots_per_s"] = out["bf16"]["snapshots_per_s_with_eig"] / out["f64"]["snapshots_per_s_with_eig"]
+    return out
 
 
 def sample_eig_accuracy(s, F, torch, N, nm, reorth=1):

@@ -53,7 +53,10 @@ typedef enum {
                               from foa_dmd_eig the stream state is unchanged and the handle
                               stays usable, after a push call the handle should be destroyed */
   FOA_DMD_EIO = 9,         /* checkpoint file error or checksum mismatch */
-  FOA_DMD_ENOCONV = 10     /* the device eigensolver did not converge */
+  FOA_DMD_ENOCONV = 10,    /* the device eigensolver did not converge */
+  FOA_DMD_ERESOLVE = 11    /* foa_dmd_push_block only: a snapshot's new direction is too small
+                              for the block form to keep V orthogonal; that snapshot and the
+                              rest of the call were not pushed, the stream is not stopped */
 } foa_dmd_status;
 
 typedef struct {
@@ -302,8 +305,19 @@ int foa_dmd_profile_read(foa_dmd_t *h, foa_dmd_kernel_stats *stats);
  *   infos: host, p results (or NULL).  The first snapshot of a stream, a remainder shorter than
  *          `block` and the columns just below k_max are pushed singly (with the handle's form).
  * A dependent snapshot inside a block commits the columns before it and stops the stream
- * (EBREAKDOWN; later snapshots ESTOPPED).  FP32/BF16 storage only (EINVAL for FP64).  The push-
- * time indicator schedule is not run by block pushes.  Synchronises the handle's stream.
+ * (EBREAKDOWN; later snapshots ESTOPPED).
+ * Resolution limit (no counterpart in the paper; Sec. 3.2.2 explains why the QR form, unlike the
+ * modified FOA update, loses accuracy as kappa_2(X) grows): block classical Gram-Schmidt keeps
+ * the new columns orthogonal to V only while a snapshot's new direction stays well above the
+ * rounding of its projections, R_ii >> u_s ||psi||.  Below R_ii = 16 u_s ||psi|| (u_s the unit
+ * roundoff of the storage type; 9.5e-7 for FP32) the block form is not used: the columns before
+ * that snapshot are committed, the call returns FOA_DMD_ERESOLVE and reports ERESOLVE for that
+ * snapshot and every later one of the call, none of which is pushed, and the stream is NOT
+ * stopped: push them with foa_dmd_push, whose modified FOA form stays orthogonal there.  (On
+ * 4 x 16^3 fields with 1e-7 noise, without this limit V lost its orthogonality about 100 columns
+ * after R_ii fell to 7 u_fp32 ||psi||, and H-bar diverged.)
+ * FP32/BF16 storage only (EINVAL for FP64).  The push-time indicator schedule is not run by block
+ * pushes.  Synchronises the handle's stream.
  */
 int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld, int32_t block,
                        foa_dmd_push_info *infos);

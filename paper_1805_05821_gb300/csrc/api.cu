@@ -105,10 +105,11 @@ static const char *kErr[] = {"ok",
                              "snapshot holds NaN or Inf",
                              "device wait timed out",
                              "checkpoint I/O error",
-                             "eigensolver did not converge"};
+                             "eigensolver did not converge",
+                             "block push cannot resolve the snapshot's new direction; push it singly"};
 
 extern "C" const char *foa_dmd_strerror(int status) {
-  if (status < 0 || status > FOA_DMD_ENOCONV) return "unknown status";
+  if (status < 0 || status > FOA_DMD_ERESOLVE) return "unknown status";
   return kErr[status];
 }
 

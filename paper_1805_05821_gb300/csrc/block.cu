@@ -26,6 +26,14 @@ namespace blk {
 
 enum BlockMode : int { BLK_A = 0, BLK_B = 1, BLK_C = 2 };
 constexpr int kMaxP = 4;
+// A block column whose new direction R_ii is below kBlockResolveUnits * u_s * ||psi|| is not
+// pushed by the block form (FOA_DMD_ERESOLVE): block CGS2 in the storage precision no longer keeps
+// such columns orthogonal to V (measured: orthogonality lost about 100 columns after R_ii reached
+// 7 u_fp32 ||psi|| on noise-floor snapshots).
+constexpr double kBlockResolveUnits = 16.0;
+__host__ __device__ inline double unit_roundoff(int dtype) {
+  return dtype == FOA_DMD_F64 ? 0x1p-53 : dtype == FOA_DMD_F32 ? 0x1p-24 : 0x1p-8;
+}
 
 struct BlockState {
   int32_t j;        // basis size before the block
@@ -56,6 +64,7 @@ struct BlockArgs {
   int32_t ntiles, kmax, j, R, slots, nstages, x_aligned;
   int32_t slot_bytes, base_off, base_stride, off_ws, off_coef, off_dot, off_comb, off_red, off_bar, smem_total;
   double tol;
+  double resolve;       // kBlockResolveUnits * u_s
 };
 
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
@@ -623,6 +632,10 @@ __global__ void __launch_bounds__(256) blockq1_kernel(BlockArgs a, foa_dmd_push_
         status = FOA_DMD_EBREAKDOWN;
         break;
       }
+      if (rii < a.resolve * bs->xnorm[i]) {  // below the block form's resolution: not committed
+        status = FOA_DMD_ERESOLVE;
+        break;
+      }
       nc = i + 1;
     }
     bs->ncommit = nc;
@@ -853,6 +866,7 @@ int enqueue_block(foa_dmd *h, BlockWork &bw, const void *X, int64_t ldx, foa_dmd
   a.j = j;
   a.x_aligned = (reinterpret_cast<uintptr_t>(X) & 15u) == 0 && ((ldx * dtype_size(h->dtype)) & 15) == 0;
   a.tol = h->tol;
+  a.resolve = kBlockResolveUnits * unit_roundoff(h->dtype);
   cudaStream_t s = h->stream;
   block_prep_kernel<<<1, 32, 0, s>>>(h->st, bw.bs, j, P, h->kmax);
   cudaError_t e = cudaGetLastError();
@@ -955,7 +969,7 @@ extern "C" int foa_dmd_push_block(foa_dmd_t *h, const void *X_dev, int32_t p, in
       if (infos)
         for (int u = t; u < p; ++u) {
           infos[u] = got[took - 1];
-          infos[u].status = FOA_DMD_ESTOPPED;
+          infos[u].status = first_bad == FOA_DMD_ERESOLVE ? FOA_DMD_ERESOLVE : FOA_DMD_ESTOPPED;
         }
       rc = first_bad;
       break;

@@ -58,35 +58,50 @@ int launch_modes(foa_dmd *h, int m, const double *Y, int ldy, int ncols, void *p
   if (h->dtype == FOA_DMD_F32 && !(simt && simt[0] == '1'))
     return launch_modes_tc(h, m, Y, ldy, ncols, static_cast<float *>(phi), ld_phi, h->eig->bop, h->eig->isc + ISC_ERR);
   const int cs = compute_size(h->dtype), s = dtype_size(h->dtype);
-  const size_t smem = ((size_t(m) * ncols * cs + 15) / 16) * 16 + size_t(kTile) * m * s;
-  if (smem > 232448) return FOA_DMD_EINVAL;
+  // A CTA keeps the m x nc block of Y and one 32 x m tile of V in shared memory.  When all ncols
+  // columns of Y do not fit (FP64 storage past m = 280 at 64 columns), the columns are split
+  // into launches of nc columns each (a multiple of 8), and V is read once per launch.
+  constexpr size_t kSmemMax = 232448;
+  const size_t vbytes = size_t(kTile) * m * s;
+  auto smem_for = [&](int nc) { return ((size_t(m) * nc * cs + 15) / 16) * 16 + vbytes; };
+  int nc_max = ncols;
+  while (nc_max > 8 && smem_for(nc_max) > kSmemMax) nc_max = (nc_max - 1) / 8 * 8;
+  if (smem_for(nc_max) > kSmemMax) return FOA_DMD_EINVAL;
   const int grid = h->ntiles < h->sms * 2 ? h->ntiles : h->sms * 2;
-  cudaError_t e;
-  switch (h->dtype) {
-    case FOA_DMD_F64:
-      e = cudaFuncSetAttribute(modes_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (e == cudaSuccess)
-        modes_simt_kernel<double><<<grid, 256, smem, h->stream>>>(static_cast<const double *>(h->V), h->kmax, h->n,
-                                                                  h->ntiles, m, Y, ldy, ncols,
-                                                                  static_cast<double *>(phi), ld_phi);
-      break;
-    case FOA_DMD_F32:
-      e = cudaFuncSetAttribute(modes_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (e == cudaSuccess)
-        modes_simt_kernel<float><<<grid, 256, smem, h->stream>>>(static_cast<const float *>(h->V), h->kmax, h->n,
-                                                                 h->ntiles, m, Y, ldy, ncols,
-                                                                 static_cast<float *>(phi), ld_phi);
-      break;
-    default:
-      e = cudaFuncSetAttribute(modes_simt_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(smem));
-      if (e == cudaSuccess)
-        modes_simt_kernel<__nv_bfloat16><<<grid, 256, smem, h->stream>>>(
-            static_cast<const __nv_bfloat16 *>(h->V), h->kmax, h->n, h->ntiles, m, Y, ldy, ncols,
-            static_cast<float *>(phi), ld_phi);
-      break;
+  const int64_t es = cs;  // phi holds the compute type (FP64 for FP64 storage, FP32 otherwise)
+  cudaError_t e = cudaSuccess;
+  for (int c0 = 0; c0 < ncols && e == cudaSuccess; c0 += nc_max) {
+    const int nc = ncols - c0 < nc_max ? ncols - c0 : nc_max;
+    const size_t smem = smem_for(nc);
+    const double *Yc = Y + int64_t(c0) * ldy;
+    void *pc = static_cast<unsigned char *>(phi) + int64_t(c0) * ld_phi * es;
+    switch (h->dtype) {
+      case FOA_DMD_F64:
+        e = cudaFuncSetAttribute(modes_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess)
+          modes_simt_kernel<double><<<grid, 256, smem, h->stream>>>(static_cast<const double *>(h->V), h->kmax, h->n,
+                                                                    h->ntiles, m, Yc, ldy, nc, static_cast<double *>(pc),
+                                                                    ld_phi);
+        break;
+      case FOA_DMD_F32:
+        e = cudaFuncSetAttribute(modes_simt_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e == cudaSuccess)
+          modes_simt_kernel<float><<<grid, 256, smem, h->stream>>>(static_cast<const float *>(h->V), h->kmax, h->n,
+                                                                   h->ntiles, m, Yc, ldy, nc, static_cast<float *>(pc),
+                                                                   ld_phi);
+        break;
+      default:
+        e = cudaFuncSetAttribute(modes_simt_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem));
+        if (e == cudaSuccess)
+          modes_simt_kernel<__nv_bfloat16><<<grid, 256, smem, h->stream>>>(
+              static_cast<const __nv_bfloat16 *>(h->V), h->kmax, h->n, h->ntiles, m, Yc, ldy, nc,
+              static_cast<float *>(pc), ld_phi);
+        break;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (c0 > 0) h->launches += 1;
   }
-  if (e == cudaSuccess) e = cudaGetLastError();
   return cuda_status(e);
 }
 

@@ -19,8 +19,8 @@ _LIB_PATH = _build.LIB
 F64, F32, BF16 = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EFULL", 5: "EBREAKDOWN", 6: "ESTOPPED",
-          7: "ENONFINITE", 8: "ETIMEOUT", 9: "EIO", 10: "ENOCONV"}
-OK, EINVAL, ENOMEM, ECUDA, EFULL, EBREAKDOWN, ESTOPPED, ENONFINITE, ETIMEOUT, EIO, ENOCONV = range(11)
+          7: "ENONFINITE", 8: "ETIMEOUT", 9: "EIO", 10: "ENOCONV", 11: "ERESOLVE"}
+OK, EINVAL, ENOMEM, ECUDA, EFULL, EBREAKDOWN, ESTOPPED, ENONFINITE, ETIMEOUT, EIO, ENOCONV, ERESOLVE = range(12)
 
 
 class foa_dmd_opts(ctypes.Structure):

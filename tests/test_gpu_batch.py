@@ -124,6 +124,6 @@ def test_batched_equals_single_stream_structure():
     F.foa_dmd_batch_destroy(b)
     assert q1 == q2 == 30
     # two FP32 summation orders: agreement to C u_fp32 kappa_2(X), like the oracle comparisons
-    tol = PARITY_C * U["f32"] * kappa_of(B1, 30)
+    tol = PARITY_C["f32"] * U["f32"] * kappa_of(B1, 30)
     assert tol <= PARITY_MAX_BOUND
     assert rel(B2, B1) <= tol and rel(H2[:30, :29], H1[:30, :29]) <= tol

@@ -57,7 +57,7 @@ def test_block_push_matches_oracle(dt, block):
         g1.push(Xd[t])
     q, _, H1, B1 = g1.state()
     kap = kappa_of(o.B, q)
-    assert rel(g.state()[3][:q, :q], B1[:q, :q]) <= PARITY_C * U[dt] * kap
+    assert rel(g.state()[3][:q, :q], B1[:q, :q]) <= PARITY_C[dt] * U[dt] * kap
 
 
 def test_block_push_breakdown_inside_a_block():
@@ -105,33 +105,60 @@ def test_block_push_on_a_two_pass_handle_and_fp64_refused():
     assert g64.push_block(x, block=4)[0] == 1  # EINVAL
 
 
-def test_block_push_wide_basis_fields():
-    """The fields workload's structure at a small grid (4 x 16^3, n = 16384), N = 160 in blocks of 4:
-    past j = 128 a pipeline stage is one 32-row tile and the row sweep splits the columns into 16
-    groups.  Against the oracle's block step; leading Ritz values against the planted ones."""
+def test_block_push_stops_at_its_resolution_limit_on_fields():
+    """The fields workload's structure at a small grid (4 x 16^3, n = 16384), N = 384, breakdown_tol
+    1e-12: after the 96 wave dimensions every snapshot adds only its 1e-7 noise (R_ii about 7 u_fp32
+    ||psi||).  Without a limit the block push lost the orthogonality of V near column 250 and
+    H-bar diverged, while reporting OK.  Now the block push stops with ERESOLVE at the first
+    snapshot whose R_ii < 16 u_fp32 ||psi||, having committed the columns before it (past j = 128,
+    where a pipeline stage is one 32-row tile and the row sweep splits the columns into 16 groups);
+    the rest go through the single push (Alg. 1 form).  V stays orthogonal and the leading Ritz
+    values match the planted eigenvalues; the block part matches the oracle's block step."""
     import torch
     from scipy.optimize import linear_sum_assignment
-    from paper_1805_05821_gb300.foa_dmd import FoaDMD
-    spec = synth.config5(0, G=16, N=160)
+    from paper_1805_05821_gb300.foa_dmd import ERESOLVE, FoaDMD
+    spec = synth.config5(0, G=16, N=384)
     X = synth.snapshots(spec, np.float32).astype(np.float64)
     Xd = torch.from_numpy(np.ascontiguousarray(X.T)).float().cuda()
-    g = FoaDMD(spec.n, 160, "f32", breakdown_tol=1e-12)
-    st, _ = g.push_block(Xd, block=4)
-    assert st == 0
-    o = oracle.FoaOracle(spec.n, 160, breakdown_tol=1e-12, storage="f32", form="qr")
-    o.push(X[:, 0])
-    for s in range(1, 160, 4):
-        o.push_block(X[:, s:s + 4])
+    g = FoaDMD(spec.n, 384, "f32", breakdown_tol=1e-12)
+    st, infos = g.push_block(Xd, block=4)
+    assert st == ERESOLVE, st
+    t0 = next(t for t, i in enumerate(infos) if i["status"] != "OK")
+    assert all(i["status"] == "ERESOLVE" for i in infos[t0:])
     q, stopped, H, B = g.state()
-    assert q == o.q == 160
+    assert q == t0 and not stopped and 128 < t0 < 250, t0
+    assert infos[t0]["x_norm"] > 0
+    # the block part against the oracle's block step on the same blocking
+    o = oracle.FoaOracle(spec.n, 384, breakdown_tol=1e-12, storage="f32", form="qr")
+    o.push(X[:, 0])
+    s = 1
+    while s + 4 <= t0:
+        o.push_block(X[:, s:s + 4])
+        s += 4
+    if s < t0:
+        o.push_block(X[:, s:t0])
+    assert o.q == t0
+    Vg = g.basis(0, q).double().cpu().numpy().T
+    assert np.linalg.norm(np.eye(q) - Vg.T @ Vg, 2) <= 1e-5
+    # normwise within the reduced-precision law (kappa_2 is large here, so this is no tight pin:
+    # the columns of the ill-conditioned part are pinned by the orthogonality check above)
+    eB = np.linalg.norm(B[:q, :q] - o.B[:q, :q]) / np.linalg.norm(o.B[:q, :q])
+    assert eB <= PARITY_C["f32"] * U["f32"] * kappa_of(o.B, q), (eB, kappa_of(o.B, q))
+    # the rest singly: the stream was not stopped
+    for t in range(t0, 384):
+        assert g.push(Xd[t], info=False)[0] == 0
+    q, stopped, H, B = g.state()
+    assert q == 384 and not stopped
     Vg = g.basis(0, q).double().cpu().numpy().T
     orth = np.linalg.norm(np.eye(q) - Vg.T @ Vg, 2)
-    assert orth <= 1e-4, orth
+    assert orth <= 1e-5, orth
     r = g.eig(-1.0)
     lam = r["lam"][:32]
     D = np.abs(lam[:, None] - spec.lam[None, :])
     ri, ci = linear_sum_assignment(D)
-    assert np.max(D[ri, ci] / np.abs(spec.lam[ci])) <= 1e-5
+    err = np.max(D[ri, ci] / np.abs(spec.lam[ci]))
+    print(f"block push stopped at {t0}; orthogonality {orth:.2e}; leading 32 vs planted {err:.2e}")
+    assert err <= 1e-6
 
 
 @pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4)])

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import scipy.linalg
 
-from gpu_util import match, rel, run_gpu, run_oracle, to_device
+from gpu_util import fp64_tol, kappa_of, match, rel, run_gpu, run_oracle, to_device
 from paper_1805_05821_gb300 import synth
 import oracle as orc
 
@@ -223,11 +223,14 @@ def test_async_indicator_records():
 
 # ---------------------------------------------------------------------------------------------
 # The eigen path at the sizes the benchmark runs: m = 383 (N = 384 snapshots of the u, v, w, p
-# fields at a reduced 16^3 grid, n = 16384, FP64 storage so that the state itself agrees with the
-# oracle to 1e-10).  The QR iteration keeps the matrix in shared memory only up to order 160, so
-# the untruncated eig (order 383) and the truncation at rank_tol = 1e-10 (every singular value
-# kept, r = 383) run its global-memory branch, the truncation at 1e-6 (r = 96, the 48 planted
-# waves) its shared-memory branch; the Jacobi SVD spans 192 CTAs.
+# fields at a reduced 16^3 grid, n = 16384, FP64 storage).  The noise of 1e-7 makes kappa_2(X)
+# about 6e7, so the state agrees with the oracle to the FP64 law max(1e-10, 4 u kappa_2) (about
+# 3e-8; measured 3e-9), and every eigen comparison uses that law with the condition number of the
+# part it works on: kappa_2(X) without truncation, sigma_1/sigma_r with it.  The QR iteration keeps
+# the matrix in shared memory only up to order 160, so the untruncated eig (order 383) and the
+# truncation at rank_tol = 1e-10 (every singular value kept, r = 383) run its global-memory
+# branch, the truncation at 1e-6 (r = 96, the 48 planted waves) its shared-memory branch; the
+# Jacobi SVD spans 192 CTAs.
 
 
 @pytest.fixture(scope="module")
@@ -239,10 +242,30 @@ def fields383():
     o, sts = run_oracle(Xr, 384, "f64", tol=1e-14)
     assert all(s[0] == 0 for s in infos) and o.q == 384
     q, _, H, B = g.state()
-    assert rel(B[:q, :q], o.B[:q, :q]) <= 1e-10
-    assert rel(H[:q, :q - 1], o.H[:q, :q - 1]) <= 1e-10
+    tol = fp64_tol(kappa_of(o.B, q))
+    assert tol <= 1e-7
+    assert rel(B[:q, :q], o.B[:q, :q]) <= tol
+    assert rel(H[:q, :q - 1], o.H[:q, :q - 1]) <= tol
     yield spec, g, o
     g.close()
+
+
+def eig_scale(o, res_o):
+    """The FP64 law's relative bound on the matrix the eigen path works on."""
+    if res_o["sigma"] is None:
+        return fp64_tol(kappa_of(o.B, o.m))
+    sig = res_o["sigma"]
+    return fp64_tol(sig[0] / sig[res_o["r"] - 1])
+
+
+def phase_distance(a, b):
+    """min over phases phi of || a/||a|| - e^{i phi} b/||b|| || (computed directly: the form
+    sqrt(2 - 2|<a, b>|) loses half the digits to cancellation)."""
+    a = a / np.linalg.norm(a)
+    b = b / np.linalg.norm(b)
+    c = np.vdot(b, a)
+    ph = c / abs(c) if abs(c) > 0 else 1.0
+    return float(np.linalg.norm(a - ph * b))
 
 
 def eigvec_tolerance(res_o, scale=1e-10):
@@ -267,22 +290,26 @@ def test_eig_full_size_branches(fields383, rank_tol, r_expect):
     ro = o.eig(rank_tol)
     assert rg["status"] == 0, rg["status"]
     assert rg["m"] == ro["m"] == 383 and rg["r"] == ro["r"] == r_expect
+    scale = eig_scale(o, ro)
     if rank_tol > 0:
-        np.testing.assert_allclose(rg["sigma"], ro["sigma"][:r_expect], rtol=1e-9)
-    perm = check_eigs(rg, ro)
-    tol_v, s_o = eigvec_tolerance(ro)
+        # singular values: |d sigma_i| <= ||d beta||_2 (Weyl), relative to sigma_1
+        assert np.all(np.abs(rg["sigma"] - ro["sigma"][:r_expect]) <= fp64_tol(kappa_of(o.B, o.m)) * ro["sigma"][0])
+    perm = check_eigs(rg, ro, scale=scale)
+    tol_v, s_o = eigvec_tolerance(ro, scale)
     good = s_o > 1e-3
-    # indicators: untruncated |h_{m+1,m}| |e_m^T z_i|, truncated the full residual norm
+    # indicators: untruncated |h_{m+1,m}| |e_m^T z_i|, truncated the full residual norm; both are
+    # Lipschitz in (H_m, h_{m+1,m}, U_r, z_i) with constant about ||H_m|| + |h_{m+1,m}|, so their
+    # first-order error is bounded by that constant times the matrix and vector perturbations
     ind_o, ind_g = ro["indicator"], rg["indicator"][perm]
     err_i = np.abs(ind_g - ind_o)
-    assert np.all(err_i[good] <= np.maximum(1e-6 * ind_o[good], 1e-9 * ind_o.max()) + tol_v[good] * ind_o.max()), \
-        np.max(err_i[good])
+    lip = np.linalg.norm(o.H[:383, :383], 2) + abs(ro["h_last"])
+    assert np.all(err_i[good] <= 10 * (tol_v[good] + scale) * lip), np.max(err_i[good] / (tol_v[good] + scale) / lip)
     # eigenvectors y_i = U_r z_i (phase-invariant) where the first-order bound is informative
     Yo, Yg = ro["Y"], rg["vec"][:, perm]
     checked = 0
     for i in np.where(good & (tol_v < 1e-4))[0]:
-        c = abs(np.vdot(Yo[:, i], Yg[:, i])) / (np.linalg.norm(Yo[:, i]) * np.linalg.norm(Yg[:, i]))
-        assert np.sqrt(max(0.0, 2 - 2 * c)) <= 10 * tol_v[i] + 1e-12, (i, c, tol_v[i])
+        d = phase_distance(Yo[:, i], Yg[:, i])
+        assert d <= 10 * tol_v[i] + 1e-12, (i, d, tol_v[i])
         checked += 1
     assert checked >= min(32, r_expect // 2), checked
     # amplitudes |c_i| of the leading 32 modes (by |c|): c = Z^-1 b depends on the whole basis Z,
@@ -290,9 +317,9 @@ def test_eig_full_size_branches(fields383, rank_tol, r_expect):
     kz = np.linalg.cond(ro["Z"])
     amp_o, amp_g = np.abs(ro["amp"]), np.abs(rg["amp"][perm])
     lead = np.arange(32)
-    assert np.all(np.abs(amp_g - amp_o)[lead] <= 1e-10 * kz * amp_o.max()), (kz, np.max(np.abs(amp_g - amp_o)[lead]))
-    print(f"m=383 rank_tol={rank_tol}: r={rg['r']}, {checked} vectors, max |dind| {np.max(err_i[good]):.2e}, "
-          f"cond(Z) {kz:.2e}")
+    assert np.all(np.abs(amp_g - amp_o)[lead] <= scale * kz * amp_o.max()), (kz, np.max(np.abs(amp_g - amp_o)[lead]))
+    print(f"m=383 rank_tol={rank_tol}: r={rg['r']}, scale {scale:.2e}, {checked} vectors, "
+          f"max |dind| {np.max(err_i[good]):.2e}, cond(Z) {kz:.2e}")
 
 
 def test_eig_full_size_modes(fields383):
@@ -301,14 +328,16 @@ def test_eig_full_size_modes(fields383):
     rg = g.eig(1e-6, n_modes=32)
     ro = o.eig(1e-6)
     assert rg["status"] == 0 and rg["r"] == 96
-    perm = check_eigs(rg, ro)
+    perm = check_eigs(rg, ro, scale=eig_scale(o, ro))
     Phi_o = o.modes(ro, 96)
     inv = np.argsort(perm)
+    # Phi_i = V y_i with V orthonormal: the mode moves by the vector's perturbation plus V's
+    scale = eig_scale(o, ro)
+    tol_v, _ = eigvec_tolerance(ro, scale)
     for k in range(32):
         i = int(inv[k])  # oracle index of the GPU's k-th mode
-        a, b = Phi_o[:, i], rg["phi"][:, k]
-        c = abs(np.vdot(a, b)) / (np.linalg.norm(a) * np.linalg.norm(b))
-        assert abs(1 - c) < 1e-8, (k, c)
+        d = phase_distance(Phi_o[:, i], rg["phi"][:, k])
+        assert d <= 10 * (tol_v[i] + scale), (k, d, tol_v[i])
 
 
 def test_indicator_records_at_large_m():
