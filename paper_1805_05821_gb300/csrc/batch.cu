@@ -1,20 +1,26 @@
 // Batched streams: one call advances every active stream of a batch by one push (Alg. 4 with
-// p = 1 per stream) in a single cooperative persistent kernel launch, capturable in a CUDA graph.
+// p = 1 per stream), as a fixed sequence of six launches that a CUDA graph can capture (every
+// per-push decision is read from device memory):
 //
-// plan_kernel (1 CTA) reads every stream's device state and the caller's pointer array and
-// builds the work list: phase 0 = beta_pre of each active stream (Alg. 1 steps 5-8), phases
-// 1-3 = the streaming passes A, B, C (steps 9-15) cut into chunks of whole pipeline stages,
-// phase 4 = the append of the new basis vector (step 15).  Items are taken from one global
-// counter in list order (phase-major).  An item of phase p of stream s starts once stream s has
-// finished phase p-1 (bounded wait); every item of phase p-1 precedes it in the list and all CTAs
-// are co-resident, so that wait always ends.  The last finisher of a (stream, phase) sums the
-// chunk partials in chunk order (deterministic) and applies the scalar part of the step.
+//   plan_kernel     reads every stream's device state and the caller's pointer array, decides
+//                   which streams push, and cuts each stream's passes into work items of whole
+//                   pipeline stages (about 8 MB of V each);
+//   prep_kernel     beta_pre of every active stream (Alg. 1 steps 5-8), one CTA per stream;
+//   bpass_kernel    pass A, then pass B, then pass C (Alg. 1 steps 9-15) of all streams, one
+//                   launch per pass: one CTA of 512 threads per SM takes items from a counter;
+//   append_kernel   v_{j+1} = w / h_{j+1,j} (Alg. 1 step 15) of every stream that pushed.
 //
-// Inside a CTA the roles are those of the single-stream warp-specialised pass: warp 8 fetches
-// items, waits for their dependencies, publishes them to the consumers through a two-deep item
-// ring and streams their stages into a shared-memory slot ring with bulk async copies; warps 0-3
-// make the row-local sweep of each stage, warps 4-7 the column dots of the previous one.  The
-// producer runs ahead into the next item while the consumers finish the current one.
+// Launch order is the only dependency between the passes of a stream, so no CTA ever waits for
+// another.  A pass item streams its stages through a three-slot shared-memory ring filled by one
+// elected thread with bulk async copies (mbarrier completion), and every thread holds a fixed row
+// pair and a fixed group of at most 16 columns of each stage in registers: from the registers it
+// forms its partial GEMV-N sums (row sweep, combined across the column groups through shared
+// memory) and, once the stage's new w is in shared memory, its columns' dot products (column
+// sweep), exactly the register-held layout of the single-stream passes.  A stage is R tiles of 32
+// rows with R = min(32, 512/j), so that R*32*j stays at 16384 elements (64 KB of FP32) and the
+// columns of a stage split into 32/R groups of at most 16.  Each item writes its FP64 partial
+// sums; the last item of a (stream, pass) adds them in item order (deterministic) and applies the
+// scalar step.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -25,11 +31,30 @@
 namespace foa {
 namespace bt {
 
-constexpr int MAX_R = 64;             // tiles per stage
-constexpr int SLOT_B = MAX_R * 32 * 4;  // base-vector bytes per slot (x or w of one stage)
-constexpr int MAX_SLOTS = 4;
-constexpr int NCB = 64;               // column accumulators per column-group lane (k_max <= 512)
-constexpr int ROW_WARPS = 4, COL_WARPS = 4, ROW_THREADS = ROW_WARPS * 32;
+constexpr int kBT = 512;                    // threads of a pass CTA (one CTA per SM)
+constexpr int kBW = kBT / 32;               // its warps
+constexpr int kFC = 16;                     // columns a thread holds in registers
+constexpr int kMaxRB = 32;                  // tiles per stage
+constexpr int kRowsMax = kMaxRB * kTile;    // rows per stage
+constexpr int kStageElems = 16384;          // R * 32 * j <= this (R = min(32, 512 / j))
+constexpr int kSlotV = kStageElems * 4;     // V bytes of a slot (FP32 worst case)
+constexpr int kSlotBase = kRowsMax * 4;     // the stage's x or w slice
+constexpr int kSlotBytes = kSlotV + kSlotBase;
+constexpr int kBSlots = 3;
+constexpr int kCf = 768;                    // padded coefficient vector (>= 32*16 + 16 + kMaxK/4)
+constexpr int64_t kItemBytes = 8ll << 20;   // V bytes per work item
+enum { PH_A = 0, PH_B = 1, PH_C = 2, PH_APP = 3, NPH = 4 };
+
+// shared-memory layout of bpass_kernel (bytes)
+constexpr size_t kOffWs = size_t(kBSlots) * kSlotBytes;
+constexpr size_t kOffCf = kOffWs + size_t(kRowsMax) * 4;
+constexpr size_t kOffComb = kOffCf + size_t(kCf) * 4;
+constexpr size_t kOffDot = kOffComb + size_t(2 * kBT) * 4;
+constexpr size_t kOffDotw = kOffDot + size_t(kMaxK + 8) * 8;
+constexpr size_t kOffNred = kOffDotw + size_t(kBW * 2 * kFC) * 8;
+constexpr size_t kOffBar = kOffNred + size_t(kBW) * 8;
+constexpr size_t kBSmem = kOffBar + size_t(kBSlots) * 8;
+static_assert(kBSmem <= 232448, "bpass_kernel shared memory");
 
 struct StreamDesc {
   int64_t n;
@@ -37,7 +62,7 @@ struct StreamDesc {
   int64_t w_off;    // element offset of w
   int64_t mat_off;  // double offset of its k_max x k_max H-bar and beta
   int64_t vec_off;  // double offset of its pre/h/s vectors (3 x k_max)
-  int64_t part_off; // double offset of its chunk partials
+  int64_t part_off; // double offset of its item partials
   int32_t ntiles;
   int32_t kmax;
   int32_t max_chunks;
@@ -50,48 +75,46 @@ struct BState {
 };
 
 struct Plan {
-  int32_t R, nstages, cs, nchunks;  // per stream (tiles per stage, stages, stages per chunk, chunks)
+  int32_t R, nstages, cs, nchunks;  // tiles per stage, stages, stages per item, items
 };
 
 struct BatchArgs {
   const StreamDesc *sd;
   BState *st;
   Plan *plan;
-  int32_t *offs;       // (5 * S + 1): item offsets, phase-major, stream-minor
-  int32_t *total;
-  uint32_t *counter;   // global work counter
-  uint32_t *tickets;   // [S][5]
-  int32_t *done;       // [S]: last finished phase (-1 before phase 0)
+  int32_t *offs;       // NPH x (S + 1): item offsets of each phase, stream-major
+  int32_t *total;      // NPH
+  uint32_t *counter;   // NPH work counters
+  uint32_t *tickets;   // S x NPH
   void *V;             // pool (storage dtype)
   float *W;            // pool of w vectors (FP32)
   double *H, *B;       // pools
   double *vec;         // pools of pre/h/s
-  double *part;        // chunk partials
+  double *part;        // item partials
   const void *const *x;  // caller's pointers (device array of S)
   double *h_last;      // caller's output array (device, S)
   double tol;
   int32_t S;
   int32_t *err;        // sticky
-  int32_t slot_v;      // V bytes per stage slot (a whole tile of the widest stream fits)
-  int32_t nslots;      // slot ring depth
-  int64_t chunk_bytes; // V bytes per work item
 };
 
-template <typename S>
-__device__ __forceinline__ float ldc(const S *p, int64_t i) {
-  return to_c(p[i]);
+// ---------------------------------------------------------------------------- plan
+__host__ __device__ __forceinline__ int stage_tiles(int j) {
+  if (j <= 0) return kMaxRB;
+  int R = 1;
+  while (R * 2 <= kMaxRB && (R * 2) * j <= kStageElems / kTile) R *= 2;
+  return R;
 }
 
-// ---------------------------------------------------------------------------- plan
 __global__ void plan_kernel(BatchArgs a, int ssize) {
   const int S = a.S;
-  extern __shared__ int32_t cnt[];  // 5 * S counts
+  extern __shared__ int32_t cnt[];  // NPH * S counts
   for (int s = threadIdx.x; s < S; s += blockDim.x) {
     const StreamDesc d = a.sd[s];
     BState &b = a.st[s];
     const bool has_x = a.x[s] != nullptr;
     const int q = b.q;
-    int active = has_x && !b.stopped && q < d.kmax;
+    const int active = has_x && !b.stopped && q < d.kmax;
     b.active = active;
     b.j = q;
     b.first = (q == 0) ? 1 : 0;
@@ -99,458 +122,346 @@ __global__ void plan_kernel(BatchArgs a, int ssize) {
     else if (has_x) b.status = b.stopped ? FOA_DMD_ESTOPPED : FOA_DMD_EFULL;
     if (a.h_last) a.h_last[s] = __longlong_as_double(0x7ff8000000000000ll);
     const int j = q;
-    const int64_t tb = int64_t(kTile) * (j > 0 ? j : 0) * ssize;
-    int R = MAX_R;
-    if (j > 0) {
-      R = 1;
-      while (R * 2 <= MAX_R && int64_t(R * 2) * tb <= a.slot_v) R *= 2;
-    }
     Plan p;
-    p.R = R;
-    p.nstages = (d.ntiles + R - 1) / R;
-    const int64_t stage_bytes = j > 0 ? int64_t(R) * tb : int64_t(R) * kTile * ssize;
-    int cs = int(a.chunk_bytes / (stage_bytes > 0 ? stage_bytes : 1));
-    if (cs < 1) cs = 1;
-    p.cs = cs;
-    p.nchunks = (p.nstages + cs - 1) / cs;
+    p.R = stage_tiles(j);
+    p.nstages = (d.ntiles + p.R - 1) / p.R;
+    const int64_t stage_bytes = int64_t(p.R) * kTile * (j > 0 ? j : 1) * ssize;
+    p.cs = int(kItemBytes / stage_bytes);
+    if (p.cs < 1) p.cs = 1;
+    p.nchunks = (p.nstages + p.cs - 1) / p.cs;
     if (p.nchunks > d.max_chunks) {  // keep within the partials buffer
       p.cs = (p.nstages + d.max_chunks - 1) / d.max_chunks;
       p.nchunks = (p.nstages + p.cs - 1) / p.cs;
     }
     a.plan[s] = p;
     const bool first = (j == 0);
-    cnt[0 * S + s] = (active && !first) ? 1 : 0;                 // beta_pre
-    cnt[1 * S + s] = active ? p.nchunks : 0;                     // pass A (or the first-snapshot norm)
-    cnt[2 * S + s] = (active && !first) ? p.nchunks : 0;         // pass B
-    cnt[3 * S + s] = (active && !first) ? p.nchunks : 0;         // pass C
-    cnt[4 * S + s] = active ? p.nchunks : 0;                     // append
-    a.done[s] = (active && !first) ? -1 : 0;  // streams without a beta_pre item start at phase 1
-    for (int ph = 0; ph < 5; ++ph) a.tickets[s * 5 + ph] = 0u;
+    cnt[PH_A * S + s] = active ? p.nchunks : 0;               // pass A (or the first snapshot's norm)
+    cnt[PH_B * S + s] = (active && !first) ? p.nchunks : 0;   // pass B
+    cnt[PH_C * S + s] = (active && !first) ? p.nchunks : 0;   // pass C
+    cnt[PH_APP * S + s] = active ? p.nchunks : 0;             // append
+    for (int ph = 0; ph < NPH; ++ph) a.tickets[s * NPH + ph] = 0u;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < NPH) {
+    const int ph = threadIdx.x;
     int run = 0;
-    for (int i = 0; i < 5 * S; ++i) {
-      a.offs[i] = run;
-      run += cnt[i];
+    for (int s = 0; s < S; ++s) {
+      a.offs[ph * (S + 1) + s] = run;
+      run += cnt[ph * S + s];
     }
-    a.offs[5 * S] = run;
-    *a.total = run;
-    *a.counter = 0u;
+    a.offs[ph * (S + 1) + S] = run;
+    a.total[ph] = run;
+    a.counter[ph] = 0u;
   }
 }
 
-// ---------------------------------------------------------------------------- helpers
-struct Item {
-  int32_t valid, stream, phase, chunk;
-};
-
-// spin (bounded) until stream s has finished phase p-1
-__device__ bool wait_phase(const BatchArgs &a, int s, int p) {
-  volatile int32_t *d = a.done + s;
-  if (*d >= p - 1) return true;
-  const long long t0 = clock64();
-  while (*d < p - 1) {
-    if (clock64() - t0 > (1ll << 33)) return false;
-    __nanosleep(200);
+// beta_pre (Alg. 1 steps 5-8): beta_pre_1 = sum_{l=1}^{j-1} h_{1,l} beta_{l,j},
+// beta_pre_i = sum_{l=i-1}^{j-1} h_{i,l} beta_{l,j}; one CTA per stream, one warp per entry.
+__global__ void prep_kernel(BatchArgs a) {
+  const int s = blockIdx.x;
+  BState *bs = a.st + s;
+  if (!bs->active || bs->first) return;
+  const StreamDesc sd = a.sd[s];
+  const int j = bs->j, K = sd.kmax;
+  const double *Hs = a.H + sd.mat_off, *Bs = a.B + sd.mat_off;
+  double *pre = a.vec + sd.vec_off;
+  if (threadIdx.x == 0) {
+    const double bjj = Bs[int64_t(j - 1) * (K + 1)];
+    bs->bjj = bjj;
+    bs->inv_bjj = 1.0 / bjj;
   }
-  return true;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < j; i += nw) {
+    const int l0 = i == 0 ? 0 : i - 1;
+    double t = 0.0;
+    for (int l = l0 + lane; l <= j - 2; l += 32) t += Hs[i + int64_t(l) * K] * Bs[l + int64_t(j - 1) * K];
+    t = warp_sum(t);
+    if (lane == 0) pre[i] = t;
+  }
 }
 
-// Decode an item index into (phase, stream, chunk) by binary search over the item offsets.
-__device__ void decode_item(const BatchArgs &a, int item, int &phase, int &stream, int &chunk) {
-  const int S = a.S;
-  int lo = 0, hi = 5 * S;
+// (phase, item) -> (stream, chunk) by binary search over the phase's item offsets
+__device__ __forceinline__ void decode_item(const BatchArgs &a, int ph, int item, int &stream, int &chunk) {
+  const int32_t *o = a.offs + ph * (a.S + 1);
+  int lo = 0, hi = a.S;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (a.offs[mid] <= item) lo = mid;
+    if (o[mid] <= item) lo = mid;
     else hi = mid;
   }
-  while (lo + 1 <= 5 * S && a.offs[lo + 1] <= item) ++lo;  // skip empty entries
-  phase = lo / S;
-  stream = lo % S;
-  chunk = item - a.offs[lo];
+  while (lo + 1 < a.S && o[lo + 1] <= item) ++lo;  // skip streams without items
+  stream = lo;
+  chunk = item - o[lo];
 }
 
+// ---------------------------------------------------------------------------- the passes
 template <typename S>
-__global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBT, 1) bpass_kernel(BatchArgs a, int ph) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const int slot_bytes = a.slot_v + SLOT_B;
-  unsigned char *slotmem = smem;                                                    // nslots x slot
-  float *wsb = reinterpret_cast<float *>(smem + size_t(a.nslots) * slot_bytes);    // 2 x MAX_R*32
-  float *cf = wsb + 2 * MAX_R * kTile;                                              // kMaxK + 8
-  double *dot = reinterpret_cast<double *>(cf + kMaxK + 8);                         // kMaxK + 2
-  float *combb = reinterpret_cast<float *>(dot + kMaxK + 2);                        // 2 x 256
-  double *nrm = reinterpret_cast<double *>(combb + 512);                            // 256
-  __shared__ uint64_t full[MAX_SLOTS], empty[MAX_SLOTS], ws_full[2], ws_empty[2], item_full[2], item_empty[2];
-  __shared__ Item ring[2];
-  __shared__ int s_abort, s_last;
+  unsigned char *slots = smem;
+  float *ws = reinterpret_cast<float *>(smem + kOffWs);       // new w of the stage's rows
+  float *cf = reinterpret_cast<float *>(smem + kOffCf);       // coefficients, zero padded
+  float *comb = reinterpret_cast<float *>(smem + kOffComb);   // row-sweep group partials
+  double *dot = reinterpret_cast<double *>(smem + kOffDot);
+  double *dotw = reinterpret_cast<double *>(smem + kOffDotw); // [warp][half][kFC] column sums
+  double *nred = reinterpret_cast<double *>(smem + kOffNred);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + kOffBar);
+  __shared__ int s_item, s_abort, s_last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kIssuer = kBT - 1;
   if (tid == 0) {
-    for (int i = 0; i < a.nslots; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kWarps);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&ws_full[b], ROW_WARPS);
-      mbar_init(&ws_empty[b], COL_WARPS);
-      mbar_init(&item_full[b], 1);
-      mbar_init(&item_empty[b], 1);
-    }
+    for (int i = 0; i < kBSlots; ++i) mbar_init(&full[i], 1);
     s_abort = 0;
     mbar_fence_init();
   }
   __syncthreads();
-  const int total = *a.total;
-  auto fail = [&]() {
-    s_abort = 1;
-    atomicExch(a.err, FOA_DMD_ETIMEOUT);
-  };
-
-  if (warp == kWarps) {
-    // ---------------------------------------------------------------- producer warp
-    if (lane != 0) return;
-    uint32_t it = 0;  // stages issued
-    for (int k = 0;; ++k) {
-      const int r = k & 1;
-      if (k >= 2 && !mbar_wait(&item_empty[r], ((k >> 1) - 1) & 1)) {
-        fail();
-        return;
-      }
-      const int item = int(atomicAdd(a.counter, 1u));
-      Item d;
-      d.valid = item < total && !s_abort;
-      if (d.valid) {
-        decode_item(a, item, d.phase, d.stream, d.chunk);
-        if (!wait_phase(a, d.stream, d.phase)) {
-          fail();
-          d.valid = 0;
-        }
-        __threadfence();  // the finished phase's results are visible to the consumers
-      }
-      ring[r] = d;
-      mbar_arrive(&item_full[r]);  // release: the descriptor
-      if (!d.valid) return;
-      if (d.phase < 1 || d.phase > 3) continue;  // beta_pre and append move no staged data
-      const StreamDesc sd = a.sd[d.stream];
-      const Plan pl = a.plan[d.stream];
-      const BState *bs = a.st + d.stream;
-      const bool first = __ldcg(&bs->first) != 0;
-      const int j = first ? 0 : __ldcg(&bs->j);
-      const int mode = first ? PASS_FIRST : (d.phase == 1 ? PASS_A : d.phase == 2 ? PASS_B : PASS_C);
-      const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
-      const S *Vs = static_cast<const S *>(a.V) + sd.v_off;
-      const S *x = static_cast<const S *>(a.x[d.stream]);
-      const float *w = a.W + sd.w_off;
-      const bool x_aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-      const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
-      const int s0 = d.chunk * pl.cs, s1 = min(pl.nstages, s0 + pl.cs);
-      for (int stg = s0; stg < s1; ++stg, ++it) {
-        const int slot = int(it % a.nslots);
-        if (it >= uint32_t(a.nslots) && !mbar_wait(&empty[slot], ((it / a.nslots) - 1) & 1)) {
-          fail();
-          return;
-        }
-        const int t0 = stg * pl.R;
-        const int nt = min(pl.R, sd.ntiles - t0);
-        const int64_t r0 = int64_t(t0) * kTile;
-        unsigned char *dst = slotmem + size_t(slot) * slot_bytes;
-        const bool bb = base_x ? (x_aligned && r0 + int64_t(nt) * kTile <= sd.n) : true;
-        const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? sizeof(S) : 4) : 0u;
-        mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
-        if (tile_bytes)
-          for (int q = 0; q < nt; ++q)
-            bulk_g2s(dst + size_t(q) * tile_bytes, Vs + int64_t(t0 + q) * sd.kmax * kTile, tile_bytes, &full[slot]);
-        if (bbytes) {
-          if (base_x) bulk_g2s(dst + a.slot_v, x + r0, bbytes, &full[slot]);
-          else bulk_g2s(dst + a.slot_v, w + r0, bbytes, &full[slot]);
-        }
-      }
-    }
-  }
-
-  // ------------------------------------------------------------------ consumer warps
-  const bool rowg = warp < ROW_WARPS;
-  uint32_t it = 0;  // stages consumed (same sequence as the producer's)
-  float acc[NCB / 2];
-  for (int k = 0;; ++k) {
-    const int r = k & 1;
-    if (!s_abort && !mbar_wait(&item_full[r], (k >> 1) & 1)) fail();
-    const Item d = ring[r];
-    named_bar_sync(1, kConsumers);  // every consumer has read the descriptor
-    if (tid == 0) mbar_arrive(&item_empty[r]);
-    if (!d.valid || s_abort) break;
-    const int sidx = d.stream, ph = d.phase, chunk = d.chunk;
+  const int total = a.total[ph];
+  uint32_t it = 0;  // stages consumed by this CTA (ring position, carried across items)
+  for (;;) {
+    if (tid == 0) s_item = s_abort ? total : int(atomicAdd(a.counter + ph, 1u));
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    int sidx, chunk;
+    decode_item(a, ph, item, sidx, chunk);
     const StreamDesc sd = a.sd[sidx];
     BState *bs = a.st + sidx;
     const Plan pl = a.plan[sidx];
-    const int j = __ldcg(&bs->j);
-    const bool first = __ldcg(&bs->first) != 0;
+    const bool first = bs->first != 0;
+    const int j = first ? 0 : bs->j;
     const int K = sd.kmax;
+    const int mode = first ? PASS_FIRST : (ph == PH_A ? PASS_A : ph == PH_B ? PASS_B : PASS_C);
+    const bool dots = (mode == PASS_A || mode == PASS_B);
+    const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
     double *Hs = a.H + sd.mat_off, *Bs = a.B + sd.mat_off;
     double *pre = a.vec + sd.vec_off, *hv = pre + K, *sv = hv + K;
-    S *Vs = static_cast<S *>(a.V) + sd.v_off;
+    const S *Vs = static_cast<const S *>(a.V) + sd.v_off;
     float *w = a.W + sd.w_off;
     const S *x = static_cast<const S *>(a.x[sidx]);
-    const int64_t nrows = int64_t(sd.ntiles) * kTile;
-
-    if (ph == 0) {
-      // ---------------------------------------------------------------- beta_pre (steps 5-8)
-      if (tid == 0) {
-        const double bjj = __ldcg(Bs + int64_t(j - 1) * (K + 1));
-        bs->bjj = bjj;
-        bs->inv_bjj = 1.0 / bjj;
-      }
-      for (int i = warp; i < j; i += kWarps) {
-        const int l0 = i == 0 ? 0 : i - 1;
-        double s_ = 0.0;
-        for (int l = l0 + lane; l <= j - 2; l += 32) s_ += __ldcg(Hs + i + int64_t(l) * K) * __ldcg(Bs + l + int64_t(j - 1) * K);
-        s_ = warp_sum(s_);
-        if (lane == 0) pre[i] = s_;
-      }
-      __threadfence();
-      named_bar_sync(1, kConsumers);
-      if (tid == 0) atomicExch(a.done + sidx, 0);
-      continue;
-    }
-    const int s0 = chunk * pl.cs;
-    const int s1 = min(pl.nstages, s0 + pl.cs);
-    if (ph == 4) {
-      // ---------------------------------------------------------------- append v_{j+1} (step 15)
-      if (__ldcg(&bs->status) == FOA_DMD_OK) {
-        const int64_t r0 = int64_t(s0) * pl.R * kTile, r1 = min(nrows, int64_t(s1) * pl.R * kTile);
-        const float sc = float(__ldcg(&bs->inv_nu));
-        for (int64_t rr = r0 + tid; rr < r1; rr += kConsumers) {
-          const float v = first ? ((rr < sd.n) ? float(to_c(x[rr])) : 0.f) : __ldcg(w + rr);
-          Vs[((rr >> 5) * K + j) * kTile + (rr & 31)] = Store<S>::from(v * sc);
-        }
-      }
-      continue;
-    }
-    // ---------------------------------------------------------------- streaming pass (A, B, C)
-    const int mode = first ? PASS_FIRST : (ph == 1 ? PASS_A : ph == 2 ? PASS_B : PASS_C);
-    const bool dots = (mode == PASS_A || mode == PASS_B);
-    const int jj = first ? 0 : j;
-    const double *coef = (mode == PASS_A) ? pre : (mode == PASS_B) ? hv : sv;
-    const float cscale = (mode == PASS_A) ? float(__ldcg(&bs->inv_bjj)) : 1.f;
-    for (int c = tid; c < ((jj + 7) & ~3); c += kConsumers) cf[c] = c < jj ? float(__ldcg(coef + c)) : 0.f;
-    for (int c = tid; c <= jj; c += kConsumers) dot[c] = 0.0;
     const bool x_aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
-    named_bar_sync(1, kConsumers);
-    if (rowg) {
-      // ------------------------------------------------------------ row group: sweep 1
-      const int rt = tid;
-      float nsum = 0.f, ncomp = 0.f;
-      auto nrm_add = [&](float v) {
-        const float y = v - ncomp;
-        const float t = nsum + y;
-        ncomp = (t - nsum) - y;
-        nsum = t;
-      };
-      for (int stg = s0; stg < s1; ++stg, ++it) {
-        const int slot = int(it % a.nslots);
-        const int b = int(it & 1);
-        if (!s_abort && !mbar_wait(&full[slot], (it / a.nslots) & 1)) fail();
-        if (it >= 2 && !s_abort && !mbar_wait(&ws_empty[b], ((it >> 1) - 1) & 1)) fail();
-        float *ws = wsb + b * (MAX_R * kTile);
-        float *cb = combb + b * 256;
-        const int t0 = stg * pl.R;
-        const int nt = min(pl.R, sd.ntiles - t0);
-        const int RS = nt * kTile;
-        const int64_t r0 = int64_t(t0) * kTile;
-        const unsigned char *sb = slotmem + size_t(slot) * slot_bytes;
-        const S *vs = reinterpret_cast<const S *>(sb);
-        const bool bb = base_x ? (x_aligned && r0 + int64_t(RS) <= sd.n) : true;
-        auto finish_row = [&](int row, float accv) {
-          const int64_t rr = r0 + row;
-          float base;
-          if (base_x) base = bb ? float(to_c(reinterpret_cast<const S *>(sb + a.slot_v)[row]))
-                                : ((rr < sd.n) ? float(to_c(x[rr])) : 0.f);
-          else base = reinterpret_cast<const float *>(sb + a.slot_v)[row];
+    const float cscale = (mode == PASS_A) ? float(bs->inv_bjj) : 1.f;
+    // the fixed mapping of this stream's stages: PF row pairs, G1 column groups of cpg columns
+    const int R = pl.R;
+    const int PF = R * (kTile / 2);
+    const int G1 = kBT / PF;
+    const int cpg = j > 0 ? ((((j + G1 - 1) / G1) + 3) & ~3) : 0;  // <= kFC since R * j <= 512
+    const double *coef = (mode == PASS_A) ? pre : (mode == PASS_B) ? hv : sv;
+    for (int c = tid; c < G1 * cpg + kFC; c += kBT) cf[c] = (c < j) ? float(coef[c]) : 0.f;
+    for (int c = tid; c <= j; c += kBT) dot[c] = 0.0;
+    for (int c = tid; c < kBW * 2 * kFC; c += kBT) dotw[c] = 0.0;
+    __syncthreads();
+    const int s0 = chunk * pl.cs, s1 = min(pl.nstages, s0 + pl.cs);
+    const int nst = s1 - s0;
+    const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
+    const int64_t tile_elems = int64_t(K) * kTile;
+    auto issue = [&](int slot, int stg) {
+      const int t0 = stg * R;
+      const int nt = min(R, sd.ntiles - t0);
+      const int64_t r0 = int64_t(t0) * kTile;
+      const bool bb = base_x ? (x_aligned && r0 + int64_t(nt) * kTile <= sd.n) : true;
+      const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? uint32_t(sizeof(S)) : 4u) : 0u;
+      unsigned char *dst = slots + size_t(slot) * kSlotBytes;
+      mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
+      if (tile_bytes)
+        for (int q = 0; q < nt; ++q)
+          bulk_g2s(dst + size_t(q) * tile_bytes, Vs + int64_t(t0 + q) * tile_elems, tile_bytes, &full[slot]);
+      if (bbytes) {
+        if (base_x) bulk_g2s(dst + kSlotV, x + r0, bbytes, &full[slot]);
+        else bulk_g2s(dst + kSlotV, w + r0, bbytes, &full[slot]);
+      }
+    };
+    if (tid == kIssuer && !s_abort)
+      for (int k = 0; k < kBSlots && k < nst; ++k) issue(int((it + k) % kBSlots), s0 + k);
+
+    const int g = tid / PF, pr = tid % PF;
+    const int c0 = g * cpg;
+    const int nc = max(0, min(j, c0 + cpg) - c0);
+    float cacc[kFC];
+#pragma unroll
+    for (int u = 0; u < kFC; ++u) cacc[u] = 0.f;
+    float nsum = 0.f, ncomp = 0.f;
+    auto nrm_add = [&](float v) {
+      const float y = v - ncomp;
+      const float t = nsum + y;
+      ncomp = (t - nsum) - y;
+      nsum = t;
+    };
+    // column sums: reduce over the lanes of the group inside the warp, then one lane per
+    // (warp, half) adds into its own FP64 accumulators
+    auto flush = [&]() {
+#pragma unroll
+      for (int u = 0; u < kFC; ++u) {
+        float v = cacc[u];
+        if (PF >= 32) v += __shfl_xor_sync(0xffffffffu, v, 16);
+#pragma unroll
+        for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((PF >= 32 ? lane == 0 : (lane & 15) == 0) && u < nc) dotw[(warp * 2 + (lane >> 4)) * kFC + u] += double(v);
+        cacc[u] = 0.f;
+      }
+    };
+    int since_flush = 0;
+    for (int k = 0; k < nst; ++k, ++it) {
+      const int stg = s0 + k;
+      const int slot = int(it % kBSlots);
+      if (!s_abort && !mbar_wait(&full[slot], (it / kBSlots) & 1)) {
+        s_abort = 1;
+        atomicExch(a.err, FOA_DMD_ETIMEOUT);
+      }
+      const int t0 = stg * R;
+      const int nt = min(R, sd.ntiles - t0);
+      const int RS = nt * kTile;
+      const int64_t r0 = int64_t(t0) * kTile;
+      const unsigned char *sbase = slots + size_t(slot) * kSlotBytes;
+      const S *vs = reinterpret_cast<const S *>(sbase);
+      const bool bb = base_x ? (x_aligned && r0 + int64_t(RS) <= sd.n) : true;
+      // ---- the thread's V fragment (two rows x nc columns) and its finish rows' base values
+      const int row = 2 * pr;
+      const bool has_rows = row < RS && j > 0;
+      float2 v[kFC];
+      {
+        const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
+#pragma unroll
+        for (int u = 0; u < kFC; ++u) v[u] = (has_rows && u < nc) ? ld_pair(vr + (c0 + u) * kTile) : make_float2(0.f, 0.f);
+      }
+      float base[kRowsMax / kBT];
+#pragma unroll
+      for (int h = 0; h < kRowsMax / kBT; ++h) {
+        const int rr = tid + h * kBT;
+        base[h] = 0.f;
+        if (rr < RS) {
+          if (base_x) base[h] = bb ? float(to_c(reinterpret_cast<const S *>(sbase + kSlotV)[rr]))
+                                   : ((r0 + rr < sd.n) ? float(to_c(x[r0 + rr])) : 0.f);
+          else base[h] = reinterpret_cast<const float *>(sbase + kSlotV)[rr];
+        }
+      }
+      // ---- row sweep from registers
+      if (j > 0) {
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+        for (int u = 0; u < kFC; u += 4) {
+          const float4 q = *reinterpret_cast<const float4 *>(cf + c0 + u);  // zero beyond j
+          a0 = fmaf(v[u].x, q.x, a0); b0 = fmaf(v[u].y, q.x, b0);
+          a1 = fmaf(v[u + 1].x, q.y, a1); b1 = fmaf(v[u + 1].y, q.y, b1);
+          a0 = fmaf(v[u + 2].x, q.z, a0); b0 = fmaf(v[u + 2].y, q.z, b0);
+          a1 = fmaf(v[u + 3].x, q.w, a1); b1 = fmaf(v[u + 3].y, q.w, b1);
+        }
+        comb[g * (2 * PF) + row] = a0 + a1;
+        comb[g * (2 * PF) + row + 1] = b0 + b1;
+      }
+      __syncthreads();  // every thread holds its fragment and base: the slot is free
+      if (tid == kIssuer && !s_abort && k + kBSlots < nst) issue(slot, stg + kBSlots);
+#pragma unroll
+      for (int h = 0; h < kRowsMax / kBT; ++h) {
+        const int rr = tid + h * kBT;
+        if (rr < RS) {
           if (mode == PASS_FIRST) {
-            nrm_add(base * base);
-            return;
+            nrm_add(base[h] * base[h]);
+          } else {
+            float acc = 0.f;
+            for (int gg = 0; gg < G1; ++gg) acc += comb[gg * (2 * PF) + rr];
+            const float wc = (mode == PASS_A) ? (base[h] - acc) * cscale : (base[h] - acc);
+            w[r0 + rr] = wc;
+            ws[rr] = wc;
+            if (mode == PASS_A) nrm_add(base[h] * base[h]);
+            else if (mode == PASS_C) nrm_add(wc * wc);
           }
-          const float wc = (mode == PASS_A) ? (base - accv) * cscale : (base - accv);
-          w[rr] = wc;
-          ws[row] = wc;
-          if (mode == PASS_A) nrm_add(base * base);
-          else if (mode == PASS_C) nrm_add(wc * wc);
-        };
-        if (jj == 0) {
-          for (int row = rt; row < RS; row += ROW_THREADS) finish_row(row, 0.f);
-        } else {
-          // row pairs, column groups of a multiple of 4, 16-byte coefficient broadcasts
-          const int P = RS >> 1;
-          const int G1 = (P >= ROW_THREADS) ? 1 : (ROW_THREADS / P);
-          if (rt < (G1 == 1 ? ROW_THREADS : G1 * P)) {
-            const int g = (G1 == 1) ? 0 : rt / P;
-            const int cpg = (((jj + G1 - 1) / G1) + 3) & ~3;
-            const int c0 = g * cpg, c1 = min(jj, c0 + cpg);
-            for (int pr = (G1 == 1 ? rt : rt % P); pr < P; pr += (G1 == 1 ? ROW_THREADS : P)) {
-              const int row = 2 * pr;
-              const S *vr = vs + (row >> 5) * (kTile * jj) + (row & 31);
-              float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-              for (int c = c0; c < c1; c += 4) {
-                const float4 q = *reinterpret_cast<const float4 *>(cf + c);
-                float2 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = (c + u < c1) ? ld_pair(vr + (c + u) * kTile) : make_float2(0.f, 0.f);
-                a0[0] = fmaf(v[0].x, q.x, a0[0]); a1[0] = fmaf(v[0].y, q.x, a1[0]);
-                a0[1] = fmaf(v[1].x, q.y, a0[1]); a1[1] = fmaf(v[1].y, q.y, a1[1]);
-                a0[2] = fmaf(v[2].x, q.z, a0[2]); a1[2] = fmaf(v[2].y, q.z, a1[2]);
-                a0[3] = fmaf(v[3].x, q.w, a0[3]); a1[3] = fmaf(v[3].y, q.w, a1[3]);
-              }
-              const float sa = (a0[0] + a0[1]) + (a0[2] + a0[3]);
-              const float sb_ = (a1[0] + a1[1]) + (a1[2] + a1[3]);
-              if (G1 > 1) {
-                cb[g * RS + row] = sa;
-                cb[g * RS + row + 1] = sb_;
-              } else {
-                finish_row(row, sa);
-                finish_row(row + 1, sb_);
-              }
-            }
-          }
-          if (G1 > 1) {
-            named_bar_sync(2, ROW_THREADS);
-            if (rt < RS) {
-              float s_ = 0.f;
-              for (int g = 0; g < G1; ++g) s_ += cb[g * RS + rt];
-              finish_row(rt, s_);
-            }
-          }
-        }
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&ws_full[b]);
-          mbar_arrive(&empty[slot]);
         }
       }
-      nrm[tid] = double(nsum) - double(ncomp);
-    } else {
-      // --------------------------------------------------------- column group: sweep 2
-      const int cw = warp - ROW_WARPS;
-      const int hl = lane & 15, half = lane >> 4;
+      __syncthreads();  // ws complete
+      // ---- column sweep from registers
+      if (dots) {
+        if (has_rows) {
+          const float2 wv = *reinterpret_cast<const float2 *>(ws + row);
 #pragma unroll
-      for (int q = 0; q < NCB / 2; ++q) acc[q] = 0.f;
-      auto flush = [&]() {
-#pragma unroll
-        for (int kk = 0; kk < NCB / 2; ++kk) {
-          const int c = cw + COL_WARPS * (2 * kk + half);
-          if (cw + COL_WARPS * (2 * kk) < jj) {  // warp-uniform
-            float v = (c < jj) ? acc[kk] : 0.f;
-#pragma unroll
-            for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (hl == 0 && c < jj) dot[c] += double(v);
-            acc[kk] = 0.f;
-          }
+          for (int u = 0; u < kFC; ++u) cacc[u] = fmaf(v[u].x, wv.x, fmaf(v[u].y, wv.y, cacc[u]));
         }
-      };
-      int since_flush = 0;
-      for (int stg = s0; stg < s1; ++stg, ++it) {
-        const int slot = int(it % a.nslots);
-        const int b = int(it & 1);
-        if (!s_abort && !mbar_wait(&full[slot], (it / a.nslots) & 1)) fail();
-        if (!s_abort && !mbar_wait(&ws_full[b], (it >> 1) & 1)) fail();
-        if (dots) {
-          const float *ws = wsb + b * (MAX_R * kTile);
-          const int t0 = stg * pl.R;
-          const int nt = min(pl.R, sd.ntiles - t0);
-          const S *vs = reinterpret_cast<const S *>(slotmem + size_t(slot) * slot_bytes);
-          for (int kt = 0; kt < nt; ++kt) {
-            const float2 wv = *reinterpret_cast<const float2 *>(ws + kt * kTile + 2 * hl);
-            const S *vt = vs + kt * (kTile * jj) + 2 * hl;
-#pragma unroll
-            for (int kk = 0; kk < NCB / 2; ++kk) {
-              const int c = cw + COL_WARPS * (2 * kk + half);
-              if (c < jj) {
-                const float2 v = ld_pair(vt + c * kTile);
-                acc[kk] = fmaf(v.x, wv.x, fmaf(v.y, wv.y, acc[kk]));
-              }
-            }
-          }
-          since_flush += nt;
-          if (since_flush >= 16) {
-            flush();
-            since_flush = 0;
-          }
-        }
-        __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&ws_empty[b]);
-          mbar_arrive(&empty[slot]);
+        if (++since_flush == 16) {  // 32 products per thread and column
+          flush();
+          since_flush = 0;
         }
       }
-      if (dots) flush();
-      nrm[tid] = 0.0;
     }
-    // ---------------------------------------------------------------- this chunk's partial
-    named_bar_sync(1, kConsumers);
+    if (dots) flush();
+    // ---- this item's partial: column sums in warp order, the norm in a fixed tree
+    double nv = double(nsum) - double(ncomp);
+    nv = warp_sum(nv);
+    if (lane == 0) nred[warp] = nv;
+    __syncthreads();
+    if (dots)
+      for (int c = tid; c < j; c += kBT) {
+        const int gc = c / cpg, u = c - gc * cpg;
+        double t = 0.0;
+        if (PF >= 32) {
+          const int w0 = gc * (PF / 32), w1 = w0 + PF / 32;
+          for (int wq = w0; wq < w1; ++wq) t += dotw[(wq * 2) * kFC + u];
+        } else {
+          t = dotw[((gc >> 1) * 2 + (gc & 1)) * kFC + u];
+        }
+        dot[c] = t;
+      }
     if (tid == 0) {
       double t = 0.0;
-      for (int i = 0; i < kConsumers; ++i) t += nrm[i];
-      dot[jj] = t;
+      for (int wq = 0; wq < kBW; ++wq) t += nred[wq];
+      dot[j] = t;
     }
-    named_bar_sync(1, kConsumers);
+    __syncthreads();
     double *pp = a.part + sd.part_off + int64_t(chunk) * (K + 1);
-    for (int c = tid; c <= jj; c += kConsumers) pp[c] = dot[c];
+    for (int c = tid; c <= j; c += kBT) pp[c] = dot[c];
     __threadfence();
-    named_bar_sync(1, kConsumers);
+    __syncthreads();
     if (tid == 0) {
-      const unsigned t = atomicAdd(a.tickets + sidx * 5 + ph, 1u);
+      const unsigned t = atomicAdd(a.tickets + sidx * NPH + ph, 1u);
       s_last = (t == unsigned(pl.nchunks - 1)) ? 1 : 0;
     }
-    named_bar_sync(1, kConsumers);
+    __syncthreads();
     if (!s_last) continue;
     __threadfence();
-    // ------------------------------------------------------------------ last chunk: reduce + scalar part
-    for (int c = tid; c <= jj; c += kConsumers) {
+    // ------------------------------------------------------------ last item: reduce + scalar step
+    for (int c = tid; c <= j; c += kBT) {
       double t = 0.0;
       for (int q = 0; q < pl.nchunks; ++q) t += __ldcg(a.part + sd.part_off + int64_t(q) * (K + 1) + c);
       dot[c] = t;
     }
-    named_bar_sync(1, kConsumers);
+    __syncthreads();
     if (mode == PASS_A) {
-      for (int c = tid; c < jj; c += kConsumers) hv[c] = dot[c];
-      if (tid == 0) bs->x_norm = sqrt(dot[jj]);
+      for (int c = tid; c < j; c += kBT) hv[c] = dot[c];
+      if (tid == 0) bs->x_norm = sqrt(dot[j]);
     } else if (mode == PASS_B) {
-      for (int c = tid; c < jj; c += kConsumers) {
+      for (int c = tid; c < j; c += kBT) {
         sv[c] = dot[c];
-        hv[c] = __ldcg(hv + c) + dot[c];
+        hv[c] = hv[c] + dot[c];
       }
     } else if (mode == PASS_C) {
-      const double nu = sqrt(dot[jj]);
-      const double xn = __ldcg(&bs->x_norm), bjj = __ldcg(&bs->bjj);
+      const double nu = sqrt(dot[j]);
+      const double xn = bs->x_norm, bjj = bs->bjj;
       int status;
       if (!isfinite(nu) || !isfinite(xn)) status = FOA_DMD_ENONFINITE;
       else if (!(nu * bjj > a.tol * xn)) status = FOA_DMD_EBREAKDOWN;
       else status = FOA_DMD_OK;
       if (status != FOA_DMD_ENONFINITE)
-        for (int c = tid; c < jj; c += kConsumers) Hs[c + int64_t(jj - 1) * K] = __ldcg(hv + c);
+        for (int c = tid; c < j; c += kBT) Hs[c + int64_t(j - 1) * K] = hv[c];
       if (status == FOA_DMD_OK)
-        for (int c = tid; c < jj; c += kConsumers) Bs[c + int64_t(jj) * K] = __ldcg(pre + c) + __ldcg(hv + c) * bjj;
-      named_bar_sync(1, kConsumers);
+        for (int c = tid; c < j; c += kBT) Bs[c + int64_t(j) * K] = pre[c] + hv[c] * bjj;
+      __syncthreads();
       if (tid == 0) {
         if (status == FOA_DMD_OK) {
-          Hs[jj + int64_t(jj - 1) * K] = nu;
-          Bs[jj + int64_t(jj) * K] = nu * bjj;
+          Hs[j + int64_t(j - 1) * K] = nu;
+          Bs[j + int64_t(j) * K] = nu * bjj;
           bs->nu = nu;
           bs->inv_nu = 1.0 / nu;
-          bs->q = jj + 1;
+          bs->q = j + 1;
           if (a.h_last) a.h_last[sidx] = nu;
         } else if (status == FOA_DMD_EBREAKDOWN) {
-          Hs[jj + int64_t(jj - 1) * K] = 0.0;
+          Hs[j + int64_t(j - 1) * K] = 0.0;
           bs->stopped = 1;
         }
         bs->h_last = nu;
         bs->status = status;
       }
-    } else {  // first snapshot
+    } else {  // first snapshot: beta_11 = ||x||
       if (tid == 0) {
         const double bn = sqrt(dot[0]);
-        int status = !isfinite(bn) ? FOA_DMD_ENONFINITE : (!(bn > 0.0) ? FOA_DMD_EBREAKDOWN : FOA_DMD_OK);
+        const int status = !isfinite(bn) ? FOA_DMD_ENONFINITE : (!(bn > 0.0) ? FOA_DMD_EBREAKDOWN : FOA_DMD_OK);
         if (status == FOA_DMD_OK) {
           Bs[0] = bn;
           bs->inv_nu = 1.0 / bn;
@@ -566,9 +477,40 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchArgs a) {
       }
     }
     __threadfence();
-    named_bar_sync(1, kConsumers);
-    // first snapshot: passes B and C do not exist, so completing the norm completes phase 3
-    if (tid == 0) atomicExch(a.done + sidx, (mode == PASS_FIRST) ? 3 : ph);
+    __syncthreads();
+  }
+}
+
+// append v_{j+1} = w / h_{j+1,j} (v_1 = x / ||x|| for a first snapshot), one item per pass item
+template <typename S>
+__global__ void append_kernel(BatchArgs a) {
+  __shared__ int s_item;
+  const int total = a.total[PH_APP];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = int(atomicAdd(a.counter + PH_APP, 1u));
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= total) return;
+    int sidx, chunk;
+    decode_item(a, PH_APP, item, sidx, chunk);
+    const BState *bs = a.st + sidx;
+    if (bs->status != FOA_DMD_OK) continue;
+    const StreamDesc sd = a.sd[sidx];
+    const Plan pl = a.plan[sidx];
+    const bool first = bs->first != 0;
+    const int j = first ? 0 : bs->j, K = sd.kmax;
+    const int64_t nrows = int64_t(sd.ntiles) * kTile;
+    const int64_t r0 = int64_t(chunk) * pl.cs * pl.R * kTile;
+    const int64_t r1 = min(nrows, int64_t(chunk + 1) * pl.cs * pl.R * kTile);
+    const float sc = float(bs->inv_nu);
+    S *Vs = static_cast<S *>(a.V) + sd.v_off;
+    const float *w = a.W + sd.w_off;
+    const S *x = static_cast<const S *>(a.x[sidx]);
+    for (int64_t rr = r0 + threadIdx.x; rr < r1; rr += blockDim.x) {
+      const float v = first ? ((rr < sd.n) ? float(to_c(x[rr])) : 0.f) : w[rr];
+      Vs[((rr >> 5) * K + j) * kTile + (rr & 31)] = Store<S>::from(v * sc);
+    }
   }
 }
 
@@ -586,21 +528,33 @@ struct foa_dmd_batch {
   StreamDesc *sd = nullptr;
   BState *st = nullptr;
   Plan *plan = nullptr;
-  int32_t *offs = nullptr, *total = nullptr, *done = nullptr, *err = nullptr;
+  int32_t *offs = nullptr, *total = nullptr, *err = nullptr;
   uint32_t *counter = nullptr, *tickets = nullptr;
   void *V = nullptr;
   float *W = nullptr;
   double *H = nullptr, *B = nullptr, *vec = nullptr, *part = nullptr;
-  size_t smem = 0;
-  int32_t slot_v = 0, nslots = 0;
-  int64_t chunk_bytes = 0;
 };
 
 static void batch_free(foa_dmd_batch *b) {
-  void *ptrs[] = {b->sd, b->st, b->plan, b->offs, b->total, b->done, b->err, b->counter, b->tickets, b->V, b->W,
+  void *ptrs[] = {b->sd, b->st, b->plan, b->offs, b->total, b->err, b->counter, b->tickets, b->V, b->W,
                   b->H, b->B, b->vec, b->part};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+}
+
+// the largest number of work items a pass of this stream can have (over every basis size j)
+static int32_t max_items(int32_t ntiles, int32_t kmax, int es) {
+  int32_t best = 1;
+  for (int j = 0; j < kmax; ++j) {
+    const int R = stage_tiles(j);
+    const int64_t nstages = (ntiles + R - 1) / R;
+    const int64_t stage_bytes = int64_t(R) * kTile * (j > 0 ? j : 1) * es;
+    int64_t cs = kItemBytes / stage_bytes;
+    if (cs < 1) cs = 1;
+    const int64_t nc = (nstages + cs - 1) / cs;
+    if (nc > best) best = int32_t(nc);
+  }
+  return best;
 }
 
 extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *k_max, int32_t dtype,
@@ -624,18 +578,6 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
   b->stream = static_cast<cudaStream_t>(o.cuda_stream);
   b->tol = o.breakdown_tol > 0.0 ? o.breakdown_tol : default_tol(dtype);
   const int es = dtype_size(dtype);
-  // a stage slot holds one whole 32-row tile of the widest stream; the ring is as deep as fits
-  int kmax_max = 2;
-  for (int s = 0; s < S; ++s) kmax_max = k_max[s] > kmax_max ? k_max[s] : kmax_max;
-  b->slot_v = int32_t((int64_t(kTile) * kmax_max * es + 127) / 128 * 128);
-  if (b->slot_v < 16384) b->slot_v = 16384;
-  const size_t fixed = size_t(2) * MAX_R * kTile * 4 + size_t(kMaxK + 8) * 4 + size_t(kMaxK + 2) * 8 + 512 * 4 +
-                       size_t(kConsumers) * 8;
-  int nslots = MAX_SLOTS;
-  while (nslots > 2 && size_t(nslots) * (b->slot_v + SLOT_B) + fixed > size_t(220) * 1024) --nslots;
-  b->nslots = nslots;
-  b->chunk_bytes = 16ll << 20;  // V bytes per work item
-  b->smem = size_t(nslots) * (b->slot_v + SLOT_B) + fixed;
   int64_t voff = 0, woff = 0, moff = 0, vecoff = 0, poff = 0;
   b->sd_host.resize(S);
   for (int s = 0; s < S; ++s) {
@@ -654,7 +596,7 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
     moff += int64_t(d.kmax) * d.kmax;
     d.vec_off = vecoff;
     vecoff += 3 * int64_t(d.kmax);
-    d.max_chunks = int32_t(int64_t(nrows) * d.kmax * es / b->chunk_bytes + 2);
+    d.max_chunks = max_items(d.ntiles, d.kmax, es);
     d.part_off = poff;
     poff += int64_t(d.max_chunks) * (d.kmax + 1);
     d.pad = 0;
@@ -667,12 +609,11 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
   BAL(b->sd, sizeof(StreamDesc) * S);
   BAL(b->st, sizeof(BState) * S);
   BAL(b->plan, sizeof(Plan) * S);
-  BAL(b->offs, sizeof(int32_t) * (5 * S + 1));
-  BAL(b->total, sizeof(int32_t));
-  BAL(b->done, sizeof(int32_t) * S);
+  BAL(b->offs, sizeof(int32_t) * NPH * (S + 1));
+  BAL(b->total, sizeof(int32_t) * NPH);
   BAL(b->err, sizeof(int32_t));
-  BAL(b->counter, sizeof(uint32_t));
-  BAL(b->tickets, sizeof(uint32_t) * 5 * S);
+  BAL(b->counter, sizeof(uint32_t) * NPH);
+  BAL(b->tickets, sizeof(uint32_t) * NPH * S);
   BAL(b->V, size_t(voff) * es);
   BAL(b->W, size_t(woff) * 4);
   BAL(b->H, size_t(moff) * 8);
@@ -688,9 +629,9 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
   if (e == cudaSuccess) e = cudaMemset(b->H, 0, size_t(moff) * 8);
   if (e == cudaSuccess) e = cudaMemset(b->B, 0, size_t(moff) * 8);
   if (e == cudaSuccess) {
-    e = cudaFuncSetAttribute(dtype == FOA_DMD_F32 ? (const void *)batch_kernel<float>
-                                                   : (const void *)batch_kernel<__nv_bfloat16>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem));
+    e = cudaFuncSetAttribute(dtype == FOA_DMD_F32 ? (const void *)bpass_kernel<float>
+                                                   : (const void *)bpass_kernel<__nv_bfloat16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBSmem));
   }
   if (e != cudaSuccess) {
     batch_free(b);
@@ -712,7 +653,6 @@ extern "C" int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, 
   a.total = b->total;
   a.counter = b->counter;
   a.tickets = b->tickets;
-  a.done = b->done;
   a.V = b->V;
   a.W = b->W;
   a.H = b->H;
@@ -724,26 +664,17 @@ extern "C" int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, 
   a.tol = b->tol;
   a.S = b->S;
   a.err = b->err;
-  a.slot_v = b->slot_v;
-  a.nslots = b->nslots;
-  a.chunk_bytes = b->chunk_bytes;
-  plan_kernel<<<1, 256, size_t(5) * b->S * 4, b->stream>>>(a, dtype_size(b->dtype));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_status(e);
-  // one CTA per SM, all co-resident (cooperative launch), so the in-kernel phase waits always end
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(b->sms);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = b->smem;
-  cfg.stream = b->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (b->dtype == FOA_DMD_F32) e = cudaLaunchKernelEx(&cfg, batch_kernel<float>, a);
-  else e = cudaLaunchKernelEx(&cfg, batch_kernel<__nv_bfloat16>, a);
-  return cuda_status(e);
+  cudaStream_t s = b->stream;
+  // the fixed launch sequence of one round: plan, beta_pre, passes A, B, C, append
+  plan_kernel<<<1, 256, size_t(NPH) * b->S * 4, s>>>(a, dtype_size(b->dtype));
+  prep_kernel<<<b->S, 256, 0, s>>>(a);
+  for (int ph = PH_A; ph <= PH_C; ++ph) {
+    if (b->dtype == FOA_DMD_F32) bpass_kernel<float><<<b->sms, kBT, kBSmem, s>>>(a, ph);
+    else bpass_kernel<__nv_bfloat16><<<b->sms, kBT, kBSmem, s>>>(a, ph);
+  }
+  if (b->dtype == FOA_DMD_F32) append_kernel<float><<<b->sms * 4, 256, 0, s>>>(a);
+  else append_kernel<__nv_bfloat16><<<b->sms * 4, 256, 0, s>>>(a);
+  return cuda_status(cudaGetLastError());
 }
 
 extern "C" int foa_dmd_batch_get_state(foa_dmd_batch_t *b, int32_t s, int32_t *q, int32_t *status, double *Hbar,

@@ -33,28 +33,30 @@ def make_streams():
     return out
 
 
-def oracle_state(Xr, k):
+def oracle_state(Xr, k, dt="f32"):
     import oracle
-    o = oracle.FoaOracle(Xr.shape[0], k, storage="f32")
+    o = oracle.FoaOracle(Xr.shape[0], k, storage=dt)
     for t in range(Xr.shape[1]):
         if o.push(Xr[:, t])[0] != "ok":
             break
     return o
 
 
-def run_batch(specs, skip, use_graph=False):
+def run_batch(specs, skip, use_graph=False, Xs=None, dt="f32"):
+    """Drive a batch round by round (graph replays or direct calls); specs give n and N, Xs (optional)
+    the n x N snapshot matrices (else the specs' synthetic snapshots)."""
     import torch
     from paper_1805_05821_gb300 import foa_dmd as F
     S = len(specs)
     devs, hosts = [], []
-    for sp in specs:
-        Xr, Xd = to_device(synth.snapshots(sp), "f32")
+    for i, sp in enumerate(specs):
+        Xr, Xd = to_device(synth.snapshots(sp) if Xs is None else Xs[i], dt)
         hosts.append(Xr)
         devs.append(Xd)
     stream = torch.cuda.Stream()
     opts = F.foa_dmd_opts_default()
     opts.cuda_stream = stream.cuda_stream
-    b = F.foa_dmd_batch_create([sp.n for sp in specs], [sp.N for sp in specs], "f32", opts)
+    b = F.foa_dmd_batch_create([sp.n for sp in specs], [sp.N for sp in specs], dt, opts)
     ptrs = torch.zeros(S, dtype=torch.int64, device="cuda")
     hl = torch.zeros(S, dtype=torch.float64, device="cuda")
     T = max(sp.N for sp in specs) + 3
@@ -127,3 +129,30 @@ def test_batched_equals_single_stream_structure():
     tol = PARITY_C["f32"] * U["f32"] * kappa_of(B1, 30)
     assert tol <= PARITY_MAX_BOUND
     assert rel(B2, B1) <= tol and rel(H2[:30, :29], H1[:30, :29]) <= tol
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_batched_wide_bases(dt):
+    """Bases up to 299 columns, so the pass items run every stage shape: R = 32 / 512 * j tiles,
+    from 32 tiles (j <= 16) down to one tile (256 < j <= 299), the column groups from one per CTA to
+    32 per CTA.  Gaussian snapshots (kappa_2 <= 1.5) of ragged lengths, one stream sitting out two
+    rounds; against the oracle column by column (C u_s kappa_2, gpu_util)."""
+    from types import SimpleNamespace
+    from paper_1805_05821_gb300 import foa_dmd as F
+    shapes = [(9001, 300), (4097, 140), (20000, 70), (777, 33)]
+    specs = [SimpleNamespace(n=n, N=N) for n, N in shapes]
+    Xs = [np.random.default_rng(50 + i).standard_normal((n, N)) for i, (n, N) in enumerate(shapes)]
+    b, hosts = run_batch(specs, {(5, 2), (6, 2)}, use_graph=True, Xs=Xs, dt=dt)
+    try:
+        for s, sp in enumerate(specs):
+            q, status, H, B = F.foa_dmd_batch_get_state(b, s, sp.N)
+            o = oracle_state(hosts[s], sp.N, dt)
+            assert q == o.q == sp.N, (s, q, o.q)
+            import torch
+            from gpu_util import torch_dtype
+            Vd = torch.empty((q, sp.n), dtype=torch_dtype(dt), device="cuda")
+            F.foa_dmd_batch_get_basis(b, s, 0, q, Vd, sp.n)
+            V = Vd.double().cpu().numpy().T
+            compare_columns(q, o.m, H, B, o, dt, V=V, label=f"batched stream {s} n={sp.n}")
+    finally:
+        F.foa_dmd_batch_destroy(b)
