@@ -7,20 +7,21 @@
 //                   pipeline stages (about 8 MB of V each);
 //   prep_kernel     beta_pre of every active stream (Alg. 1 steps 5-8), one CTA per stream;
 //   bpass_kernel    pass A, then pass B, then pass C (Alg. 1 steps 9-15) of all streams, one
-//                   launch per pass: one CTA of 512 threads per SM takes items from a counter;
+//                   launch per pass: two CTAs of 256 threads per SM take items from a counter;
 //   append_kernel   v_{j+1} = w / h_{j+1,j} (Alg. 1 step 15) of every stream that pushed.
 //
 // Launch order is the only dependency between the passes of a stream, so no CTA ever waits for
-// another.  A pass item streams its stages through a three-slot shared-memory ring filled by one
-// elected thread with bulk async copies (mbarrier completion), and every thread holds a fixed row
-// pair and a fixed group of at most 16 columns of each stage in registers: from the registers it
-// forms its partial GEMV-N sums (row sweep, combined across the column groups through shared
-// memory) and, once the stage's new w is in shared memory, its columns' dot products (column
-// sweep), exactly the register-held layout of the single-stream passes.  A stage is R tiles of 32
-// rows with R = min(32, 512/j), so that R*32*j stays at 16384 elements (64 KB of FP32) and the
-// columns of a stage split into 32/R groups of at most 16.  Each item writes its FP64 partial
-// sums; the last item of a (stream, pass) adds them in item order (deterministic) and applies the
-// scalar step.
+// another.  A pass item streams its stages through a shared-memory ring (two to six slots, as many
+// stages as 100 KB holds) filled by one elected thread with bulk async copies (mbarrier
+// completion), and every thread holds a fixed row pair and a fixed group of at most 16 (32 when a
+// stage is one tile of more than 256 columns) columns of each stage in registers: from the
+// registers it forms its partial GEMV-N sums (row sweep, combined across the column groups through
+// shared memory) and, once the stage's new w is in shared memory, its columns' dot products
+// (column sweep): the register-held layout of the single-stream passes, with two CTAs of 256
+// threads per SM so that one CTA's barriers overlap the other's work.  A stage is R tiles of 32
+// rows, R the largest power of two <= 8 with R*j <= 256 (stages of up to 32 KB of FP32, three to a
+// ring), or one tile when j > 256.  Each item writes its FP64 partial sums; the last item of a (stream, pass)
+// adds them in item order (deterministic) and applies the scalar step.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -31,30 +32,28 @@
 namespace foa {
 namespace bt {
 
-constexpr int kBT = 512;                    // threads of a pass CTA (one CTA per SM)
+constexpr int kBT = 256;                    // threads of a pass CTA (two CTAs per SM)
 constexpr int kBW = kBT / 32;               // its warps
-constexpr int kFC = 16;                     // columns a thread holds in registers
-constexpr int kMaxRB = 32;                  // tiles per stage
+constexpr int kMaxRB = 8;                   // tiles per stage
 constexpr int kRowsMax = kMaxRB * kTile;    // rows per stage
-constexpr int kStageElems = 16384;          // R * 32 * j <= this (R = min(32, 512 / j))
-constexpr int kSlotV = kStageElems * 4;     // V bytes of a slot (FP32 worst case)
-constexpr int kSlotBase = kRowsMax * 4;     // the stage's x or w slice
-constexpr int kSlotBytes = kSlotV + kSlotBase;
-constexpr int kBSlots = 3;
-constexpr int kCf = 768;                    // padded coefficient vector (>= 32*16 + 16 + kMaxK/4)
-constexpr int64_t kItemBytes = 8ll << 20;   // V bytes per work item
+constexpr int kStageCols = 256;             // R * j <= this while R > 1: stages of <= 32 KB (FP32)
+constexpr int kRingBytes = 102400;          // the stage ring of a CTA (two 50 KB slots hold j <= 399)
+constexpr int kMaxBSlots = 6;
+constexpr int kCf = 640;                    // padded coefficient vector (>= 16 * 32 + 32)
+constexpr int64_t kItemBytes = 8ll << 20;   // V bytes per work item ...
+constexpr int kItemStages = 256;            // ... and at most this many stages
 enum { PH_A = 0, PH_B = 1, PH_C = 2, PH_APP = 3, NPH = 4 };
 
-// shared-memory layout of bpass_kernel (bytes)
-constexpr size_t kOffWs = size_t(kBSlots) * kSlotBytes;
+// shared-memory layout of bpass_kernel (bytes); two CTAs share an SM's 228 KB
+constexpr size_t kOffWs = size_t(kRingBytes);
 constexpr size_t kOffCf = kOffWs + size_t(kRowsMax) * 4;
 constexpr size_t kOffComb = kOffCf + size_t(kCf) * 4;
 constexpr size_t kOffDot = kOffComb + size_t(2 * kBT) * 4;
 constexpr size_t kOffDotw = kOffDot + size_t(kMaxK + 8) * 8;
-constexpr size_t kOffNred = kOffDotw + size_t(kBW * 2 * kFC) * 8;
+constexpr size_t kOffNred = kOffDotw + size_t(kBW * 16) * 8;
 constexpr size_t kOffBar = kOffNred + size_t(kBW) * 8;
-constexpr size_t kBSmem = kOffBar + size_t(kBSlots) * 8;
-static_assert(kBSmem <= 232448, "bpass_kernel shared memory");
+constexpr size_t kBSmem = kOffBar + size_t(kMaxBSlots) * 8;
+static_assert(2 * (kBSmem + 1024 + 64) <= 233472, "two bpass_kernel CTAs per SM");
 
 struct StreamDesc {
   int64_t n;
@@ -102,7 +101,7 @@ struct BatchArgs {
 __host__ __device__ __forceinline__ int stage_tiles(int j) {
   if (j <= 0) return kMaxRB;
   int R = 1;
-  while (R * 2 <= kMaxRB && (R * 2) * j <= kStageElems / kTile) R *= 2;
+  while (R * 2 <= kMaxRB && (R * 2) * j <= kStageCols) R *= 2;
   return R;
 }
 
@@ -127,6 +126,7 @@ __global__ void plan_kernel(BatchArgs a, int ssize) {
     p.nstages = (d.ntiles + p.R - 1) / p.R;
     const int64_t stage_bytes = int64_t(p.R) * kTile * (j > 0 ? j : 1) * ssize;
     p.cs = int(kItemBytes / stage_bytes);
+    if (p.cs > kItemStages) p.cs = kItemStages;
     if (p.cs < 1) p.cs = 1;
     p.nchunks = (p.nstages + p.cs - 1) / p.cs;
     if (p.nchunks > d.max_chunks) {  // keep within the partials buffer
@@ -195,28 +195,185 @@ __device__ __forceinline__ void decode_item(const BatchArgs &a, int ph, int item
 }
 
 // ---------------------------------------------------------------------------- the passes
+// Per-item constants of the stage loop.
+struct ItemGeo {
+  int R, PF, G1, cpg, c0, nc, g, pr, ns;
+  uint32_t tile_bytes, base_off, slot_bytes;
+  int64_t tile_elems;
+};
+
+// The stages [s0, s1) of one item: per stage, the thread's V fragment (two rows x nc <= FC columns)
+// goes to registers, the row sweep's group partials to comb, the finished rows' w to global and
+// shared memory, and the column sweep's products to FP32 accumulators folded every 16 stages into
+// FP64 (dot for column groups inside a warp, dotw per warp for groups that span several warps).
+template <typename S, int FC>
+__device__ __forceinline__ void run_stages(const BatchArgs &a, const StreamDesc &sd, const ItemGeo &ig, int mode,
+                                           int j, int s0, int s1, float cscale, const S *x, float *w,
+                                           unsigned char *slots, uint64_t *full, float *ws, const float *cf,
+                                           float *comb, double *dot, double *dotw, uint32_t &par, int &s_abort,
+                                           float &nsum, float &ncomp) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kIssuer = kBT - 1;
+  const bool dots = (mode == PASS_A || mode == PASS_B);
+  const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
+  const bool x_aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+  const S *Vs = static_cast<const S *>(a.V) + sd.v_off;
+  const int R = ig.R, PF = ig.PF, G1 = ig.G1, c0 = ig.c0, nc = ig.nc, g = ig.g, ns = ig.ns;
+  auto issue = [&](int slot, int stg) {
+    const int t0 = stg * R;
+    const int nt = min(R, sd.ntiles - t0);
+    const int64_t r0 = int64_t(t0) * kTile;
+    const bool bb = base_x ? (x_aligned && r0 + int64_t(nt) * kTile <= sd.n) : true;
+    const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? uint32_t(sizeof(S)) : 4u) : 0u;
+    unsigned char *dst = slots + size_t(slot) * ig.slot_bytes;
+    mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * ig.tile_bytes + bbytes);
+    if (ig.tile_bytes)
+      for (int q = 0; q < nt; ++q)
+        bulk_g2s(dst + size_t(q) * ig.tile_bytes, Vs + int64_t(t0 + q) * ig.tile_elems, ig.tile_bytes, &full[slot]);
+    if (bbytes) {
+      if (base_x) bulk_g2s(dst + ig.base_off, x + r0, bbytes, &full[slot]);
+      else bulk_g2s(dst + ig.base_off, w + r0, bbytes, &full[slot]);
+    }
+  };
+  const int nst = s1 - s0;
+  if (tid == kIssuer && !s_abort)
+    for (int k = 0; k < ns && k < nst; ++k) issue(k, s0 + k);
+  float cacc[FC];
+#pragma unroll
+  for (int u = 0; u < FC; ++u) cacc[u] = 0.f;
+  auto nrm_add = [&](float v) {
+    const float y = v - ncomp;
+    const float t = nsum + y;
+    ncomp = (t - nsum) - y;
+    nsum = t;
+  };
+  auto flush = [&]() {
+#pragma unroll
+    for (int u = 0; u < FC; ++u) {
+      float v = cacc[u];
+      if (PF >= 32) v += __shfl_xor_sync(0xffffffffu, v, 16);
+#pragma unroll
+      for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (u < nc) {
+        if (PF <= 32) {
+          if ((lane & (PF - 1)) == 0) dot[c0 + u] += double(v);   // the group is this warp or half-warp
+        } else if (lane == 0) {
+          dotw[warp * 16 + u] += double(v);                       // FC == 16 here (R >= 4)
+        }
+      }
+      cacc[u] = 0.f;
+    }
+  };
+  int since_flush = 0;
+  for (int k = 0; k < nst; ++k) {
+    const int stg = s0 + k;
+    const int slot = k % ns;
+    if (!s_abort && !mbar_wait(&full[slot], (par >> slot) & 1u)) {
+      s_abort = 1;
+      atomicExch(a.err, FOA_DMD_ETIMEOUT);
+    }
+    par ^= 1u << slot;
+    const int t0 = stg * R;
+    const int nt = min(R, sd.ntiles - t0);
+    const int RS = nt * kTile;
+    const int64_t r0 = int64_t(t0) * kTile;
+    const unsigned char *sbase = slots + size_t(slot) * ig.slot_bytes;
+    const S *vs = reinterpret_cast<const S *>(sbase);
+    const bool bb = base_x ? (x_aligned && r0 + int64_t(RS) <= sd.n) : true;
+    // ---- the thread's V fragment and its finish rows' base values
+    const int row = 2 * ig.pr;
+    const bool has_rows = row < RS && j > 0;
+    float2 v[FC];
+    {
+      const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
+#pragma unroll
+      for (int u = 0; u < FC; ++u) v[u] = (has_rows && u < nc) ? ld_pair(vr + (c0 + u) * kTile) : make_float2(0.f, 0.f);
+    }
+    float base[kRowsMax / kBT];
+#pragma unroll
+    for (int h = 0; h < kRowsMax / kBT; ++h) {
+      const int rr = tid + h * kBT;
+      base[h] = 0.f;
+      if (rr < RS) {
+        if (base_x) base[h] = bb ? float(to_c(reinterpret_cast<const S *>(sbase + ig.base_off)[rr]))
+                                 : ((r0 + rr < sd.n) ? float(to_c(x[r0 + rr])) : 0.f);
+        else base[h] = reinterpret_cast<const float *>(sbase + ig.base_off)[rr];
+      }
+    }
+    // ---- row sweep from registers
+    if (j > 0) {
+      float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+      for (int u = 0; u < FC; u += 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(cf + c0 + u);  // zero beyond j
+        a0 = fmaf(v[u].x, q.x, a0); b0 = fmaf(v[u].y, q.x, b0);
+        a1 = fmaf(v[u + 1].x, q.y, a1); b1 = fmaf(v[u + 1].y, q.y, b1);
+        a0 = fmaf(v[u + 2].x, q.z, a0); b0 = fmaf(v[u + 2].y, q.z, b0);
+        a1 = fmaf(v[u + 3].x, q.w, a1); b1 = fmaf(v[u + 3].y, q.w, b1);
+      }
+      comb[g * (2 * PF) + row] = a0 + a1;
+      comb[g * (2 * PF) + row + 1] = b0 + b1;
+    }
+    __syncthreads();  // every thread holds its fragment and base: the slot is free
+    if (tid == kIssuer && !s_abort && k + ns < nst) issue(slot, stg + ns);
+#pragma unroll
+    for (int h = 0; h < kRowsMax / kBT; ++h) {
+      const int rr = tid + h * kBT;
+      if (rr < RS) {
+        if (mode == PASS_FIRST) {
+          nrm_add(base[h] * base[h]);
+        } else {
+          float acc = 0.f;
+          for (int gg = 0; gg < G1; ++gg) acc += comb[gg * (2 * PF) + rr];
+          const float wc = (mode == PASS_A) ? (base[h] - acc) * cscale : (base[h] - acc);
+          w[r0 + rr] = wc;
+          ws[rr] = wc;
+          if (mode == PASS_A) nrm_add(base[h] * base[h]);
+          else if (mode == PASS_C) nrm_add(wc * wc);
+        }
+      }
+    }
+    __syncthreads();  // ws complete
+    // ---- column sweep from registers
+    if (dots) {
+      if (has_rows) {
+        const float2 wv = *reinterpret_cast<const float2 *>(ws + row);
+#pragma unroll
+        for (int u = 0; u < FC; ++u) cacc[u] = fmaf(v[u].x, wv.x, fmaf(v[u].y, wv.y, cacc[u]));
+      }
+      if (++since_flush == 16) {  // 32 products per thread and column
+        flush();
+        since_flush = 0;
+      }
+    }
+  }
+  if (dots) flush();
+}
+
 template <typename S>
-__global__ void __launch_bounds__(kBT, 1) bpass_kernel(BatchArgs a, int ph) {
+__global__ void __launch_bounds__(kBT, 2) bpass_kernel(BatchArgs a, int ph) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *slots = smem;
   float *ws = reinterpret_cast<float *>(smem + kOffWs);       // new w of the stage's rows
   float *cf = reinterpret_cast<float *>(smem + kOffCf);       // coefficients, zero padded
   float *comb = reinterpret_cast<float *>(smem + kOffComb);   // row-sweep group partials
   double *dot = reinterpret_cast<double *>(smem + kOffDot);
-  double *dotw = reinterpret_cast<double *>(smem + kOffDotw); // [warp][half][kFC] column sums
+  double *dotw = reinterpret_cast<double *>(smem + kOffDotw); // [warp][16] column sums (R >= 4)
   double *nred = reinterpret_cast<double *>(smem + kOffNred);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + kOffBar);
   __shared__ int s_item, s_abort, s_last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  constexpr int kIssuer = kBT - 1;
   if (tid == 0) {
-    for (int i = 0; i < kBSlots; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < kMaxBSlots; ++i) mbar_init(&full[i], 1);
     s_abort = 0;
     mbar_fence_init();
   }
   __syncthreads();
   const int total = a.total[ph];
-  uint32_t it = 0;  // stages consumed by this CTA (ring position, carried across items)
+  // Ring slots are laid out per item (as many stages of the item's size as the ring holds): an
+  // item starts with an empty ring, so only the barriers' phases carry over: bit b of par is the
+  // parity barrier b completes next (every thread waits on the same barriers in the same order).
+  uint32_t par = 0u;
   for (;;) {
     if (tid == 0) s_item = s_abort ? total : int(atomicAdd(a.counter + ph, 1u));
     __syncthreads();
@@ -232,171 +389,53 @@ __global__ void __launch_bounds__(kBT, 1) bpass_kernel(BatchArgs a, int ph) {
     const int K = sd.kmax;
     const int mode = first ? PASS_FIRST : (ph == PH_A ? PASS_A : ph == PH_B ? PASS_B : PASS_C);
     const bool dots = (mode == PASS_A || mode == PASS_B);
-    const bool base_x = (mode == PASS_A || mode == PASS_FIRST);
     double *Hs = a.H + sd.mat_off, *Bs = a.B + sd.mat_off;
     double *pre = a.vec + sd.vec_off, *hv = pre + K, *sv = hv + K;
-    const S *Vs = static_cast<const S *>(a.V) + sd.v_off;
     float *w = a.W + sd.w_off;
     const S *x = static_cast<const S *>(a.x[sidx]);
-    const bool x_aligned = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
     const float cscale = (mode == PASS_A) ? float(bs->inv_bjj) : 1.f;
     // the fixed mapping of this stream's stages: PF row pairs, G1 column groups of cpg columns
-    const int R = pl.R;
-    const int PF = R * (kTile / 2);
-    const int G1 = kBT / PF;
-    const int cpg = j > 0 ? ((((j + G1 - 1) / G1) + 3) & ~3) : 0;  // <= kFC since R * j <= 512
+    ItemGeo ig;
+    ig.R = pl.R;
+    ig.PF = ig.R * (kTile / 2);
+    ig.G1 = kBT / ig.PF;
+    ig.cpg = j > 0 ? ((((j + ig.G1 - 1) / ig.G1) + 3) & ~3) : 0;  // <= 16, or <= 32 when R = 1
+    ig.g = tid / ig.PF;
+    ig.pr = tid % ig.PF;
+    ig.c0 = ig.g * ig.cpg;
+    ig.nc = max(0, min(j, ig.c0 + ig.cpg) - ig.c0);
+    ig.tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
+    ig.tile_elems = int64_t(K) * kTile;
+    ig.base_off = uint32_t(ig.R) * ig.tile_bytes;                           // 16-byte multiple
+    ig.slot_bytes = (ig.base_off + uint32_t(ig.R) * kTile * 4u + 127u) & ~127u;
+    ig.ns = int(uint32_t(kRingBytes) / ig.slot_bytes);
+    if (ig.ns > kMaxBSlots) ig.ns = kMaxBSlots;                              // >= 1 (j < 400: >= 2)
     const double *coef = (mode == PASS_A) ? pre : (mode == PASS_B) ? hv : sv;
-    for (int c = tid; c < G1 * cpg + kFC; c += kBT) cf[c] = (c < j) ? float(coef[c]) : 0.f;
+    const int fcmax = ig.cpg > 16 ? 32 : 16;
+    for (int c = tid; c < ig.G1 * ig.cpg + fcmax; c += kBT) cf[c] = (c < j) ? float(coef[c]) : 0.f;
     for (int c = tid; c <= j; c += kBT) dot[c] = 0.0;
-    for (int c = tid; c < kBW * 2 * kFC; c += kBT) dotw[c] = 0.0;
+    for (int c = tid; c < kBW * 16; c += kBT) dotw[c] = 0.0;
     __syncthreads();
     const int s0 = chunk * pl.cs, s1 = min(pl.nstages, s0 + pl.cs);
-    const int nst = s1 - s0;
-    const uint32_t tile_bytes = uint32_t(kTile) * uint32_t(j) * sizeof(S);
-    const int64_t tile_elems = int64_t(K) * kTile;
-    auto issue = [&](int slot, int stg) {
-      const int t0 = stg * R;
-      const int nt = min(R, sd.ntiles - t0);
-      const int64_t r0 = int64_t(t0) * kTile;
-      const bool bb = base_x ? (x_aligned && r0 + int64_t(nt) * kTile <= sd.n) : true;
-      const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? uint32_t(sizeof(S)) : 4u) : 0u;
-      unsigned char *dst = slots + size_t(slot) * kSlotBytes;
-      mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
-      if (tile_bytes)
-        for (int q = 0; q < nt; ++q)
-          bulk_g2s(dst + size_t(q) * tile_bytes, Vs + int64_t(t0 + q) * tile_elems, tile_bytes, &full[slot]);
-      if (bbytes) {
-        if (base_x) bulk_g2s(dst + kSlotV, x + r0, bbytes, &full[slot]);
-        else bulk_g2s(dst + kSlotV, w + r0, bbytes, &full[slot]);
-      }
-    };
-    if (tid == kIssuer && !s_abort)
-      for (int k = 0; k < kBSlots && k < nst; ++k) issue(int((it + k) % kBSlots), s0 + k);
-
-    const int g = tid / PF, pr = tid % PF;
-    const int c0 = g * cpg;
-    const int nc = max(0, min(j, c0 + cpg) - c0);
-    float cacc[kFC];
-#pragma unroll
-    for (int u = 0; u < kFC; ++u) cacc[u] = 0.f;
     float nsum = 0.f, ncomp = 0.f;
-    auto nrm_add = [&](float v) {
-      const float y = v - ncomp;
-      const float t = nsum + y;
-      ncomp = (t - nsum) - y;
-      nsum = t;
-    };
-    // column sums: reduce over the lanes of the group inside the warp, then one lane per
-    // (warp, half) adds into its own FP64 accumulators
-    auto flush = [&]() {
-#pragma unroll
-      for (int u = 0; u < kFC; ++u) {
-        float v = cacc[u];
-        if (PF >= 32) v += __shfl_xor_sync(0xffffffffu, v, 16);
-#pragma unroll
-        for (int o = 8; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((PF >= 32 ? lane == 0 : (lane & 15) == 0) && u < nc) dotw[(warp * 2 + (lane >> 4)) * kFC + u] += double(v);
-        cacc[u] = 0.f;
-      }
-    };
-    int since_flush = 0;
-    for (int k = 0; k < nst; ++k, ++it) {
-      const int stg = s0 + k;
-      const int slot = int(it % kBSlots);
-      if (!s_abort && !mbar_wait(&full[slot], (it / kBSlots) & 1)) {
-        s_abort = 1;
-        atomicExch(a.err, FOA_DMD_ETIMEOUT);
-      }
-      const int t0 = stg * R;
-      const int nt = min(R, sd.ntiles - t0);
-      const int RS = nt * kTile;
-      const int64_t r0 = int64_t(t0) * kTile;
-      const unsigned char *sbase = slots + size_t(slot) * kSlotBytes;
-      const S *vs = reinterpret_cast<const S *>(sbase);
-      const bool bb = base_x ? (x_aligned && r0 + int64_t(RS) <= sd.n) : true;
-      // ---- the thread's V fragment (two rows x nc columns) and its finish rows' base values
-      const int row = 2 * pr;
-      const bool has_rows = row < RS && j > 0;
-      float2 v[kFC];
-      {
-        const S *vr = vs + (row >> 5) * (kTile * j) + (row & 31);
-#pragma unroll
-        for (int u = 0; u < kFC; ++u) v[u] = (has_rows && u < nc) ? ld_pair(vr + (c0 + u) * kTile) : make_float2(0.f, 0.f);
-      }
-      float base[kRowsMax / kBT];
-#pragma unroll
-      for (int h = 0; h < kRowsMax / kBT; ++h) {
-        const int rr = tid + h * kBT;
-        base[h] = 0.f;
-        if (rr < RS) {
-          if (base_x) base[h] = bb ? float(to_c(reinterpret_cast<const S *>(sbase + kSlotV)[rr]))
-                                   : ((r0 + rr < sd.n) ? float(to_c(x[r0 + rr])) : 0.f);
-          else base[h] = reinterpret_cast<const float *>(sbase + kSlotV)[rr];
-        }
-      }
-      // ---- row sweep from registers
-      if (j > 0) {
-        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-#pragma unroll
-        for (int u = 0; u < kFC; u += 4) {
-          const float4 q = *reinterpret_cast<const float4 *>(cf + c0 + u);  // zero beyond j
-          a0 = fmaf(v[u].x, q.x, a0); b0 = fmaf(v[u].y, q.x, b0);
-          a1 = fmaf(v[u + 1].x, q.y, a1); b1 = fmaf(v[u + 1].y, q.y, b1);
-          a0 = fmaf(v[u + 2].x, q.z, a0); b0 = fmaf(v[u + 2].y, q.z, b0);
-          a1 = fmaf(v[u + 3].x, q.w, a1); b1 = fmaf(v[u + 3].y, q.w, b1);
-        }
-        comb[g * (2 * PF) + row] = a0 + a1;
-        comb[g * (2 * PF) + row + 1] = b0 + b1;
-      }
-      __syncthreads();  // every thread holds its fragment and base: the slot is free
-      if (tid == kIssuer && !s_abort && k + kBSlots < nst) issue(slot, stg + kBSlots);
-#pragma unroll
-      for (int h = 0; h < kRowsMax / kBT; ++h) {
-        const int rr = tid + h * kBT;
-        if (rr < RS) {
-          if (mode == PASS_FIRST) {
-            nrm_add(base[h] * base[h]);
-          } else {
-            float acc = 0.f;
-            for (int gg = 0; gg < G1; ++gg) acc += comb[gg * (2 * PF) + rr];
-            const float wc = (mode == PASS_A) ? (base[h] - acc) * cscale : (base[h] - acc);
-            w[r0 + rr] = wc;
-            ws[rr] = wc;
-            if (mode == PASS_A) nrm_add(base[h] * base[h]);
-            else if (mode == PASS_C) nrm_add(wc * wc);
-          }
-        }
-      }
-      __syncthreads();  // ws complete
-      // ---- column sweep from registers
-      if (dots) {
-        if (has_rows) {
-          const float2 wv = *reinterpret_cast<const float2 *>(ws + row);
-#pragma unroll
-          for (int u = 0; u < kFC; ++u) cacc[u] = fmaf(v[u].x, wv.x, fmaf(v[u].y, wv.y, cacc[u]));
-        }
-        if (++since_flush == 16) {  // 32 products per thread and column
-          flush();
-          since_flush = 0;
-        }
-      }
-    }
-    if (dots) flush();
-    // ---- this item's partial: column sums in warp order, the norm in a fixed tree
+    if (ig.cpg > 16)
+      run_stages<S, 32>(a, sd, ig, mode, j, s0, s1, cscale, x, w, slots, full, ws, cf, comb, dot, dotw, par,
+                        s_abort, nsum, ncomp);
+    else
+      run_stages<S, 16>(a, sd, ig, mode, j, s0, s1, cscale, x, w, slots, full, ws, cf, comb, dot, dotw, par,
+                        s_abort, nsum, ncomp);
+    // ---- this item's partial: column sums (warp order for groups that span warps), the norm in a
+    // fixed tree
     double nv = double(nsum) - double(ncomp);
     nv = warp_sum(nv);
     if (lane == 0) nred[warp] = nv;
     __syncthreads();
-    if (dots)
+    if (dots && ig.PF > 32)
       for (int c = tid; c < j; c += kBT) {
-        const int gc = c / cpg, u = c - gc * cpg;
+        const int gc = c / ig.cpg, u = c - gc * ig.cpg;
+        const int w0 = gc * (ig.PF / 32), w1 = w0 + ig.PF / 32;
         double t = 0.0;
-        if (PF >= 32) {
-          const int w0 = gc * (PF / 32), w1 = w0 + PF / 32;
-          for (int wq = w0; wq < w1; ++wq) t += dotw[(wq * 2) * kFC + u];
-        } else {
-          t = dotw[((gc >> 1) * 2 + (gc & 1)) * kFC + u];
-        }
+        for (int wq = w0; wq < w1; ++wq) t += dotw[wq * 16 + u];
         dot[c] = t;
       }
     if (tid == 0) {
@@ -550,6 +589,7 @@ static int32_t max_items(int32_t ntiles, int32_t kmax, int es) {
     const int64_t nstages = (ntiles + R - 1) / R;
     const int64_t stage_bytes = int64_t(R) * kTile * (j > 0 ? j : 1) * es;
     int64_t cs = kItemBytes / stage_bytes;
+    if (cs > kItemStages) cs = kItemStages;
     if (cs < 1) cs = 1;
     const int64_t nc = (nstages + cs - 1) / cs;
     if (nc > best) best = int32_t(nc);
@@ -629,9 +669,9 @@ extern "C" int foa_dmd_batch_create(int32_t S, const int64_t *n, const int32_t *
   if (e == cudaSuccess) e = cudaMemset(b->H, 0, size_t(moff) * 8);
   if (e == cudaSuccess) e = cudaMemset(b->B, 0, size_t(moff) * 8);
   if (e == cudaSuccess) {
-    e = cudaFuncSetAttribute(dtype == FOA_DMD_F32 ? (const void *)bpass_kernel<float>
-                                                   : (const void *)bpass_kernel<__nv_bfloat16>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBSmem));
+    const void *kern = dtype == FOA_DMD_F32 ? (const void *)bpass_kernel<float> : (const void *)bpass_kernel<__nv_bfloat16>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kBSmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   if (e != cudaSuccess) {
     batch_free(b);
@@ -669,8 +709,8 @@ extern "C" int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, 
   plan_kernel<<<1, 256, size_t(NPH) * b->S * 4, s>>>(a, dtype_size(b->dtype));
   prep_kernel<<<b->S, 256, 0, s>>>(a);
   for (int ph = PH_A; ph <= PH_C; ++ph) {
-    if (b->dtype == FOA_DMD_F32) bpass_kernel<float><<<b->sms, kBT, kBSmem, s>>>(a, ph);
-    else bpass_kernel<__nv_bfloat16><<<b->sms, kBT, kBSmem, s>>>(a, ph);
+    if (b->dtype == FOA_DMD_F32) bpass_kernel<float><<<2 * b->sms, kBT, kBSmem, s>>>(a, ph);
+    else bpass_kernel<__nv_bfloat16><<<2 * b->sms, kBT, kBSmem, s>>>(a, ph);
   }
   if (b->dtype == FOA_DMD_F32) append_kernel<float><<<b->sms * 4, 256, 0, s>>>(a);
   else append_kernel<__nv_bfloat16><<<b->sms * 4, 256, 0, s>>>(a);
