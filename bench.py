@@ -6,7 +6,7 @@ stored in FP32 (V is 103 GB), 48 damped travelling waves with amplitudes 1 -> 1e
 relative noise (kappa_2(X) near 1/eps_fp32).  One step is one full streaming run: reset,
 384 pushes (Alg. 4 with p = 1, the error indicator evaluated every 16 pushes over the 32
 leading modes), then the eigen-decomposition with automatic rank truncation and the DMD modes
-Phi for the 32 leading modes (Alg. 1 steps 20-29).  The snapshots are generated on the device
+Phi for the 32 leading modes (the eigen extraction of Alg. 1).  The snapshots are generated on the device
 before timing (103 GB, larger than L2, so no flush is needed between steps).
 
 Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead.
@@ -39,7 +39,7 @@ FALLBACK_HBM_GBS = 6800.0
 BREAKDOWN_TOL = 1e-12
 PASS_NAMES = {1: ("A", "B", "C", "other"), 2: ("A2 (lagged append + first projection)", "B2 (second projection + commit)",
                                             "unused", "other")}
-PUSH_FORM = {1: "CGS2, three passes over V per push (Alg. 1 steps 9-15)",
+PUSH_FORM = {1: "CGS2, three passes over V per push (pre-vector, CGS2 projections and norm of Alg. 1)",
              2: "CGS2 read as two passes over V per push (h_{j+1,j} by Pythagoras, lagged append)"}
 
 
@@ -60,8 +60,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="skip the launch-geometry autotuner (untimed setup)")
     p.add_argument("--no-variants", action="store_true",
-                   help="skip the secondary lines: the two-pass push on the same workload and the FP64/FP32/BF16 "
-                        "storage forms on the 1024^2 waves")
+                   help="skip the secondary lines: the two-pass push on the same workload, the 256 batched "
+                        "streams and the FP64/FP32/BF16 storage forms on the 1024^2 waves")
     p.add_argument("--sample-grid", type=int, default=40, help="grid of the CPU-oracle sample")
     p.add_argument("--workload", default="fields", choices=["fields", "batched", "forms", "waves3d"],
                    help="fields: the 4-field 256^3 stream (default); batched: 256 uneven planted streams; "
@@ -69,6 +69,10 @@ def parse():
                         "(kappa_t 1e4) through the three-pass push and the block push of 4")
     p.add_argument("--reps", type=int, default=2, help="waves3d: timed repetitions of each push form")
     p.add_argument("--streams", type=int, default=256)
+    p.add_argument("--batch-n", type=int, default=0,
+                   help="batched: give every stream this length (planted rank 16, noise 1e-5) instead of the "
+                        "log-uniform mix; a small case for profiling")
+    p.add_argument("--batch-snapshots", type=int, default=0, help="batched with --batch-n: snapshots per stream")
     return p.parse_args()
 
 
@@ -383,10 +387,15 @@ def main():
         phi = None
         torch.cuda.empty_cache()
         out["variants"] = {"two_pass": run_variant(args, spec, X, n, N, F, L, world, 2)}
-    # ---- the storage forms on the 1024^2 waves (rank 0 of a one-rank run)
+    # ---- the batched streams and the storage forms (rank 0 of a one-rank run)
     if not args.no_variants and rank == 0 and world == 1:
+        if h is not None:
+            F.foa_dmd_destroy(h)
+            h = None
+        phi = X = tabs = coefs = None  # the 256 streams' bases take 174 GB
         torch.cuda.empty_cache()
-        out.setdefault("variants", {})["forms"] = run_forms_variant(F, torch)
+        out.setdefault("variants", {})["batched"] = batched_measure(args.streams)
+        out["variants"]["forms"] = run_forms_variant(F, torch)
     # ---- CPU oracle baseline (rank 0) and the FP32-vs-FP64 eigenvalue error on that sample
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(args.sample_grid, N, args.indicator_every, nm, n, args.reorth)
@@ -573,17 +582,22 @@ def sample_eig_accuracy(s, F, torch, N, nm, reorth=1):
     return {"sample_leading32_eig_rel_err_vs_fp64_oracle": err, "sample_rank_gpu": res["r"], "sample_rank_oracle": ro["r"]}
 
 
-def run_batched(args):
-    """Secondary measurement: S independent planted streams (n log-uniform in [2^14, 2^22], N in
-    [50, 400], FP32) advanced together by foa_dmd_batch_push, one cooperative persistent launch per
-    round captured in a CUDA graph.  The snapshots of all streams do not fit in HBM next to their
-    bases, so each round's snapshots are generated on the device before the round and only the
-    graph replays are timed (CUDA events)."""
+def batched_measure(streams=256, n_fixed=0, N_fixed=0):
+    """The batched streams (config 4): S independent planted streams (n log-uniform in [2^14, 2^22],
+    N in [50, 400], rank 8-32, noise 1e-5, FP32) advanced together by foa_dmd_batch_push, one round
+    (plan, beta_pre, passes A/B/C over all streams, append) captured once in a CUDA graph and
+    replayed per round.  The snapshots of all streams do not fit in HBM next to their bases, so
+    each round's snapshots are generated on the device before the round and only the replays are
+    timed (CUDA events on the batch's stream).  Algorithmic bytes: the V bytes of the three passes,
+    3 n j 4 per push."""
     import torch
     from paper_1805_05821_gb300 import build, synth
     from paper_1805_05821_gb300 import foa_dmd as F
     build.build()
-    specs = synth.config4(0, streams=args.streams)
+    if n_fixed:
+        specs = [synth.planted(n_fixed, N_fixed, 16, seed=1000 + s, noise_rel=1e-5) for s in range(streams)]
+    else:
+        specs = synth.config4(0, streams=streams)
     S = len(specs)
     stream = torch.cuda.Stream()
     opts = F.foa_dmd_opts_default()
@@ -621,16 +635,27 @@ def run_batched(args):
         total_ms += e0.elapsed_time(e1)
     statuses = [F.foa_dmd_batch_get_state(b, s, specs[s].N)[1] for s in range(S)]
     F.foa_dmd_batch_destroy(b)
+    del bufs, coefs, graph
+    torch.cuda.empty_cache()
     peak, _ = measured_peak()
     achieved = bytes_alg / (total_ms / 1e3) / 1e9
-    line = {"metric": "snapshots/s over 256 uneven streams (batched push)", "value": pushes / (total_ms / 1e3),
-            "unit": "snapshots/s", "n_gpus": 1, "rounds": rounds, "pushes": pushes, "ms_total": total_ms,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{S} planted streams, n log-uniform [2^14,2^22], N U[50,400], rank 8-32, "
-                                   "noise 1e-5, FP32; one graph replay per round"},
+    return {"metric": f"snapshots/s over {S} uneven streams (batched push)", "value": pushes / (total_ms / 1e3),
+            "unit": "snapshots/s", "rounds": rounds, "pushes": pushes, "ms_total": total_ms,
+            "workload": (f"{S} planted streams, n = {n_fixed}, N = {N_fixed}, rank 16, noise 1e-5, FP32" if n_fixed else
+                         f"{S} planted streams, n log-uniform [2^14,2^22], N U[50,400], rank 8-32, noise 1e-5, FP32")
+                        + "; one graph replay per round (6 launches: plan, beta_pre, passes A/B/C, append)",
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "note": "V bytes of the three passes per push over the replay time"},
+                         "kernel": "bpass_kernel (passes A, B, C of all streams)",
+                         "note": "V bytes of the three passes per push (3 n j 4) over the replay time"},
+            "gpu_launches": 6 * rounds,
             "streams_ok": int(sum(1 for st in statuses if st == 0))}
+
+
+def run_batched(args):
+    """Secondary measurement printed on its own (see batched_measure)."""
+    line = batched_measure(args.streams, args.batch_n, args.batch_snapshots)
+    line.update({"n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                 "config": {"workload": line.pop("workload")}})
     print(json.dumps(line), flush=True)
     return 0
 

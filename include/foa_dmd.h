@@ -4,7 +4,7 @@
  * The library implements the modified Full Orthogonalization Arnoldi (FOA) update of
  * FOA-based projected DMD (Anantharamu & Mahesh, arXiv:1805.05821, Sec. 3.1, Algorithms 1,
  * 3 and 4) and the on-demand extraction of DMD eigenvalues, error indicators, amplitudes and
- * modes (Algorithm 1 steps 20-29, Sec. 3.2.2-3.2.4).  Every step runs in CUDA kernels built
+ * modes (the eigen extraction of Algorithm 1, Sec. 3.2.2-3.2.4).  Every step runs in CUDA kernels built
  * for sm_103a; there is no CPU fallback.  If no suitable GPU is present, foa_dmd_create
  * returns FOA_DMD_ECUDA.
  *
@@ -61,7 +61,7 @@ typedef enum {
 
 typedef struct {
   int32_t reorth;          /* 1 (default): classical Gram-Schmidt with one reorthogonalization
-                              (CGS2, Alg. 1 steps 10-14); 0: one classical Gram-Schmidt pass;
+                              (CGS2, Alg. 1); 0: one classical Gram-Schmidt pass;
                               2: the same CGS2 step read as two passes over V per push:
                               h_{j+1,j} from ||w||^2 - ||s||^2 (w after the first projection,
                               s = V^T w, Pythagoras for orthonormal V), and v_{j+1} written
@@ -78,7 +78,7 @@ typedef struct {
   double indicator_rank_tol; /* rank_tol for the scheduled eigensolve (0: no truncation,
                                 < 0: automatic, as for foa_dmd_eig) */
   void *cuda_stream;       /* cudaStream_t for all work of the handle; NULL = default stream */
-  int32_t form;            /* 0 (default): the push as Alg. 1 steps 5-18 print it (pre-vector
+  int32_t form;            /* 0 (default): the push as Alg. 1 prints it (pre-vector
                               w = (psi - V beta_pre)/beta_jj, beta column from beta_pre + h beta_jj);
                               1: the QR view of the same push (Sec. 3.1): psi is orthogonalised
                               directly (h = V^T psi, CGS2 or CGS1 as reorth says), the beta column
@@ -105,15 +105,15 @@ typedef struct {
 /*
  * Create a stream of snapshots of length n with room for k_max snapshots
  * (2 <= k_max <= 512).  Allocates V (n x k_max, storage dtype, row-tiled), H-bar and beta
- * (k_max x k_max, FP64) and scratch on the current device (Alg. 4 step 2 done once, at the
- * maximum size).  opts may be NULL (defaults).  Errors: EINVAL, ENOMEM, ECUDA.
+ * (k_max x k_max, FP64) and scratch on the current device (the allocation of Alg. 4 done once, at
+ * the maximum size).  opts may be NULL (defaults).  Errors: EINVAL, ENOMEM, ECUDA.
  */
 int foa_dmd_create(int64_t n, int32_t k_max, int32_t dtype, const foa_dmd_opts *opts,
                    foa_dmd_t **out);
 
 /*
- * Push one snapshot: Algorithm 4 with p = 1 (Alg. 1 steps 2-3 for the first snapshot, steps
- * 5-18 otherwise).  x_dev: device, n contiguous elements of the handle's dtype, 16-byte
+ * Push one snapshot: Algorithm 4 with p = 1 (the first snapshot's normalisation, otherwise
+ * the modified FOA update of Alg. 1).  x_dev: device, n contiguous elements of the handle's dtype, 16-byte
  * aligned.  info: host; NULL makes the call fully asynchronous (no synchronisation), and
  * errors found on the device are then reported by the next synchronising call.  The first
  * push of a stream always synchronises.  Errors: EINVAL, EFULL, EBREAKDOWN, ESTOPPED,
@@ -157,7 +157,7 @@ int foa_dmd_indicators(foa_dmd_t *h, int32_t *push_index, int32_t *m, double *va
 int foa_dmd_sync(foa_dmd_t *h, foa_dmd_push_info *info);
 
 /*
- * Eigen-decomposition of the projected matrix (Alg. 1 steps 20-29, Alg. 3 steps 5-14), all
+ * Eigen-decomposition of the projected matrix (the eigen extraction of Alg. 1 and Alg. 3), all
  * on the device in FP64:
  *   m = q-1 (or q after a breakdown), H_m = H-bar(1:m,1:m);
  *   rank_tol > 0: SVD beta_m = U Sigma W^T, r = #{sigma_i > rank_tol sigma_1},
@@ -170,7 +170,7 @@ int foa_dmd_sync(foa_dmd_t *h, foa_dmd_push_info *info);
  *   amplitudes c (Sec. 3.2.4, Eqs. exrecon/exreconwrt): [z] c = beta_11 U_r^T e_1;
  *   order: |c| descending, then |lambda| descending, then Im(lambda) descending
  *   (a conjugate pair shares the larger |c|, so its +Im member comes first);
- *   modes (Alg. 1 step 26): Phi_i = V_{1:m} U_r z_i for the first n_modes in that order.
+ *   modes (Alg. 1): Phi_i = V_{1:m} U_r z_i for the first n_modes in that order.
  * Results go to the caller's buffers in res (see foa_dmd_eig_result).  Synchronises.
  * Errors: EINVAL (m < 1, cap too small, bad phi buffer), ENOCONV, ECUDA.
  */
@@ -274,8 +274,8 @@ const char *foa_dmd_strerror(int status);
 /*
  * Kernel timing.  While enabled, every streaming-pass launch of the handle is bracketed by
  * CUDA events on the handle's stream.  foa_dmd_profile_read synchronises and returns, per
- * kernel kind (0: pass A = Alg. 1 steps 9-10, 1: pass B = steps 11-12, 2: pass C = steps
- * 13-15, 3: column write of step 15; with reorth = 2, 0 is the lagged first pass, 1 the second
+ * kernel kind (0: pass A = pre-vector and h = V^T w, 1: pass B = w -= V h and s = V^T w, 2: pass
+ * C = h += s, w -= V s and ||w||, 3: the column write v_{j+1} = w / h_{j+1,j}; with reorth = 2, 0 is the lagged first pass, 1 the second
  * pass and 3 also the finishing column write), the summed event time in ms, the launch count and the
  * algorithmic bytes those launches had to move, plus the number of kernels of any kind the
  * handle launched since the previous read, then clears the counters.

@@ -5,11 +5,12 @@ leg use this package; the product path (``paper_1805_05821_gb300``) never import
 imports nothing from the product except the shared seeded input generators.
 
 * ``FoaOracle.push`` is the streaming update of Algorithm 4 (one snapshot, p = 1) carried out by
-  the plain C code in ``foa_oracle.c`` (Algorithm 1 steps 2-19, unfused, fixed-order sums).
-* ``FoaOracle.eig`` is Algorithm 1 steps 20-29 / Algorithm 3 steps 5-14: the projected matrix
+  the plain C code in ``foa_oracle.c`` (the basis and coefficient updates of Algorithm 1, unfused,
+  fixed-order sums).
+* ``FoaOracle.eig`` is the eigen extraction of Algorithms 1 and 3: the projected matrix
   H_m, the optional SVD of beta_m and rank truncation, the eigenpairs (LAPACK through scipy),
   the error indicators of Sec. 3.2.3 and the amplitudes of Sec. 3.2.4, Eqs. (exrecon)/(exreconwrt).
-* ``FoaOracle.modes`` forms the DMD modes V U_r z_i (Algorithm 1 step 26).
+* ``FoaOracle.modes`` forms the DMD modes V U_r z_i (Algorithm 1).
 
 Every function names the passage it follows; where the paper is silent or ambiguous, the docstring
 states the reading taken.
@@ -94,7 +95,7 @@ class FoaOracle:
     """Streaming FOA-based DMD state (H, V, beta, q) of Algorithm 3 in FP64 on the host."""
 
     def __init__(self, n, k_max, breakdown_tol=None, storage="f64", reorth=1, library=None, form="foa"):
-        """form: "foa" = Alg. 1 steps 5-18 as printed; "qr" = the QR view of the same push
+        """form: "foa" = the modified FOA update of Alg. 1; "qr" = the QR view of the same push
         (psi orthogonalised directly, beta column = [h; nu], Hbar column from Eq. matmulhbeta)."""
         assert form in ("foa", "qr")
         self.form = form
@@ -197,7 +198,7 @@ class FoaOracle:
                 break
         return res
 
-    # Algorithm 1 steps 20-29 / Algorithm 3 steps 5-14
+    # the eigen extraction of Algorithms 1 and 3
     @property
     def m(self):
         """Size of the projected matrix: q-1 normally, q after a breakdown (Sec. 3.2.4)."""
@@ -253,7 +254,7 @@ class FoaOracle:
                 "h_last": hlast}
 
     def modes(self, res, n_modes):
-        """DMD modes V_{1:m} U_r z_i for the first n_modes in the returned order (Alg. 1 step 26)."""
+        """DMD modes V_{1:m} U_r z_i for the first n_modes in the returned order (Alg. 1)."""
         m = res["m"]
         return self.V[:, :m] @ res["Y"][:, :n_modes]
 

@@ -1,6 +1,6 @@
 /*
  * FP64 CPU oracle of the modified Full Orthogonalization Arnoldi (FOA) update of FOA-based
- * DMD (Anantharamu & Mahesh, arXiv:1805.05821): Algorithm 1 steps 2-19 and the streaming
+ * DMD (Anantharamu & Mahesh, arXiv:1805.05821): the basis and coefficient updates of Algorithm 1 and the streaming
  * update of Algorithm 4, one snapshot per call.
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links or calls this file; only the
@@ -82,7 +82,7 @@ static void gemv_n(int64_t n, int32_t j, const double *V, int64_t ldv, const dou
 }
 
 /*
- * First push (Alg. 4 steps 4-8 / Alg. 1 steps 2-3): beta_{1,1} = ||psi_1||_2,
+ * First push (Algorithms 1 and 4): beta_{1,1} = ||psi_1||_2,
  * v_1 = psi_1 / beta_{1,1}.  Returns ORACLE_BREAKDOWN for a zero snapshot.
  */
 int foa_oracle_first(int64_t n, double *V, double *B, const double *x, double *out_norm) {
@@ -98,15 +98,17 @@ int foa_oracle_first(int64_t n, double *V, double *B, const double *x, double *o
 }
 
 /*
- * One modified-FOA step with j = q >= 1 basis vectors (Alg. 4 steps 9-20 for one snapshot,
- * Alg. 1 steps 4-18 for index j):
- *   beta_pre_1     = sum_{l=1}^{j-1}   h_{1,l} beta_{l,j}                     (step 5)
- *   beta_pre_i     = sum_{l=i-1}^{j-1} h_{i,l} beta_{l,j},  i = 2..j          (steps 6-8)
- *   w              = (psi_{j+1} - V_{1:j} beta_pre) / beta_{j,j}               (step 9)
- *   h              = V^T w;  w = w - V h;  s = V^T w;  h = h + s;  w = w - V s (steps 10-14)
- *   h_{j+1,j}      = ||w||_2;  v_{j+1} = w / h_{j+1,j}                           (step 15)
- *   beta_{i,j+1}   = beta_pre_i + h_{i,j} beta_{j,j},  i = 1..j;
- *   beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}                                       (steps 16-18)
+ * One modified-FOA update of Algorithm 1 (Algorithm 4 for one snapshot) with j = q >= 1 basis
+ * vectors.  With the stored basis V (n x j, orthonormal), H-bar (upper Hessenberg) and beta (upper
+ * triangular, X_{1:j} = V beta), the snapshot psi = psi_{j+1} is taken into the basis through the
+ * scaled pre-vector of the last column, not through psi itself (Sec. 3.1):
+ *   beta_pre  = H-bar_{1:j,1:j-1} beta_{1:j-1,j}, i.e. beta_pre_i = sum_{l=max(1,i-1)}^{j-1} h_{i,l} beta_{l,j}
+ *               (H-bar is upper Hessenberg; beta_pre = 0 for j = 1)
+ *   w         = (psi - V beta_pre) / beta_{j,j}
+ *   h         = V^T w,  w = w - V h,  s = V^T w,  h = h + s,  w = w - V s    (CGS with one reorthogonalisation)
+ *   h_{j+1,j} = ||w||_2,  v_{j+1} = w / h_{j+1,j}
+ *   beta_{1:j,j+1} = beta_pre + h beta_{j,j},  beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}
+ * so that psi = V_{1:j+1} beta_{1:j+1,j+1} and H-bar gains column j = [h; h_{j+1,j}].
  * reorth = 0 drops the second Gram-Schmidt pass (s = 0, classical Gram-Schmidt once).
  * reorth = 2 is the two-pass reading of the same step: h_{j+1,j} is taken from the Pythagorean
  * identity ||w - V s||^2 = ||w||^2 - ||s||^2 (w after the first projection, s = V^T w), the form
@@ -133,34 +135,31 @@ int foa_oracle_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, int
 #define BT(i, l) B[(int64_t)(l) * ldb + (i)]
   const int32_t jc = j - 1; /* 0-based index of column j */
 
-  /* steps 5-8: beta_pre (empty sums give 0 when j = 1) */
+  /* beta_pre (empty sums give 0 when j = 1) */
   for (int32_t i = 0; i < j; ++i) {
     int32_t l0 = i == 0 ? 0 : i - 1;
     double acc = 0.0;
     for (int32_t l = l0; l <= j - 2; ++l) acc += HB(i, l) * BT(l, jc);
     pre[i] = acc;
   }
-  /* step 9 */
+  /* the scaled pre-vector */
   double bjj = BT(jc, jc);
   gemv_n(n, j, V, ldv, pre, y);
   for (int64_t r = 0; r < n; ++r) w[r] = (x[r] - y[r]) / bjj;
-  /* step 10 */
+  /* first projection */
   gemv_t(n, j, V, ldv, w, h, part);
-  /* step 11 */
   gemv_n(n, j, V, ldv, h, y);
   for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];
   double w1norm2 = 0.0;
   if (reorth == 2) w1norm2 = dot_blocked(n, w, w, part);
   if (reorth) {
-    /* step 12 */
+    /* reorthogonalisation */
     gemv_t(n, j, V, ldv, w, s, part);
-    /* step 13 */
     for (int32_t i = 0; i < j; ++i) h[i] = h[i] + s[i];
-    /* step 14 */
     gemv_n(n, j, V, ldv, s, y);
     for (int64_t r = 0; r < n; ++r) w[r] = w[r] - y[r];
   }
-  /* step 15 */
+  /* the new direction's norm h_{j+1,j} */
   double nu;
   if (reorth == 2) {
     double ss = 0.0;
@@ -182,7 +181,7 @@ int foa_oracle_step(int64_t n, int32_t j, double *V, int64_t ldv, double *H, int
     HB(j, jc) = nu;
     double *vn = V + (int64_t)j * ldv;
     for (int64_t r = 0; r < n; ++r) vn[r] = w[r] / nu;
-    /* steps 16-18 */
+    /* the beta column */
     for (int32_t i = 0; i < j; ++i) BT(i, j) = pre[i] + h[i] * bjj;
     BT(j, j) = nu * bjj;
   }

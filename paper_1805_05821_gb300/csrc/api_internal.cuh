@@ -2,6 +2,8 @@
 #pragma once
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 namespace foa {
@@ -77,13 +79,16 @@ struct foa_dmd {
 };
 
 namespace foa {
-// Record an event pair around a pass launch when profiling.
+// An NVTX range names every streaming-pass launch (for tools: ncu --nvtx --nvtx-include "foa_dmd pass B/"
+// selects the B passes); while profiling is enabled, a CUDA event pair also brackets the launch.
 struct ProfScope {
   foa_dmd *h;
   int kind;
   double bytes;
   size_t idx;
   ProfScope(foa_dmd *h_, int kind_, double bytes_) : h(h_), kind(kind_), bytes(bytes_), idx(size_t(-1)) {
+    static const char *kNames[4] = {"foa_dmd pass A", "foa_dmd pass B", "foa_dmd pass C", "foa_dmd column write"};
+    nvtxRangePushA(kNames[kind & 3]);
     if (!h->prof) return;
     if (h->prof_used == h->events.size()) {
       EventPair p;
@@ -98,6 +103,7 @@ struct ProfScope {
   }
   ~ProfScope() {
     if (idx != size_t(-1)) cudaEventRecord(h->events[idx].stop, h->stream);
+    nvtxRangePop();
   }
 };
 

@@ -5,10 +5,10 @@
 //   plan_kernel     reads every stream's device state and the caller's pointer array, decides
 //                   which streams push, and cuts each stream's passes into work items of whole
 //                   pipeline stages (about 8 MB of V each);
-//   prep_kernel     beta_pre of every active stream (Alg. 1 steps 5-8), one CTA per stream;
-//   bpass_kernel    pass A, then pass B, then pass C (Alg. 1 steps 9-15) of all streams, one
+//   prep_kernel     beta_pre of every active stream (Alg. 1), one CTA per stream;
+//   bpass_kernel    pass A, then pass B, then pass C (pre-vector, CGS2, norm; Alg. 1) of all streams, one
 //                   launch per pass: two CTAs of 256 threads per SM take items from a counter;
-//   append_kernel   v_{j+1} = w / h_{j+1,j} (Alg. 1 step 15) of every stream that pushed.
+//   append_kernel   v_{j+1} = w / h_{j+1,j} (Alg. 1) of every stream that pushed.
 //
 // Launch order is the only dependency between the passes of a stream, so no CTA ever waits for
 // another.  A pass item streams its stages through a shared-memory ring (two to six slots, as many
@@ -155,7 +155,7 @@ __global__ void plan_kernel(BatchArgs a, int ssize) {
   }
 }
 
-// beta_pre (Alg. 1 steps 5-8): beta_pre_1 = sum_{l=1}^{j-1} h_{1,l} beta_{l,j},
+// beta_pre (Alg. 1): beta_pre_1 = sum_{l=1}^{j-1} h_{1,l} beta_{l,j},
 // beta_pre_i = sum_{l=i-1}^{j-1} h_{i,l} beta_{l,j}; one CTA per stream, one warp per entry.
 __global__ void prep_kernel(BatchArgs a) {
   const int s = blockIdx.x;
@@ -705,6 +705,7 @@ extern "C" int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, 
   a.S = b->S;
   a.err = b->err;
   cudaStream_t s = b->stream;
+  nvtxRangePushA("foa_dmd batch push");
   // the fixed launch sequence of one round: plan, beta_pre, passes A, B, C, append
   plan_kernel<<<1, 256, size_t(NPH) * b->S * 4, s>>>(a, dtype_size(b->dtype));
   prep_kernel<<<b->S, 256, 0, s>>>(a);
@@ -714,6 +715,7 @@ extern "C" int foa_dmd_batch_push(foa_dmd_batch_t *b, const void *const *x_dev, 
   }
   if (b->dtype == FOA_DMD_F32) append_kernel<float><<<b->sms * 4, 256, 0, s>>>(a);
   else append_kernel<__nv_bfloat16><<<b->sms * 4, 256, 0, s>>>(a);
+  nvtxRangePop();
   return cuda_status(cudaGetLastError());
 }
 

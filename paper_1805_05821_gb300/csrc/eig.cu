@@ -1,4 +1,4 @@
-// Device eigen path of FOA-based DMD (Alg. 1 steps 20-29, Alg. 3 steps 5-14), all in FP64:
+// Device eigen path of FOA-based DMD (the eigen extraction of Alg. 1 and Alg. 3), all in FP64:
 //
 //   svd_jacobi_kernel  one-sided (Hestenes) Jacobi SVD of the upper-triangular beta_m, run by a
 //                      cooperative grid: each round of the round-robin ordering rotates m/2

@@ -184,7 +184,15 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
 }
 
 // Synchronous eigen path on the handle's stream; copies the sorted scalars back.
+static int run_eig_body(foa_dmd *h, double rank_tol, int nsel, EigOut &res);
 static int run_eig(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
+  nvtxRangePushA("foa_dmd eig");
+  const int rc = run_eig_body(h, rank_tol, nsel, res);
+  nvtxRangePop();
+  return rc;
+}
+
+static int run_eig_body(foa_dmd *h, double rank_tol, int nsel, EigOut &res) {
   int rc = sync_state(h, nullptr);
   if (rc) return rc;
   const int q = h->q_host;

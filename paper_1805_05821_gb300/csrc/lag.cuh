@@ -1,4 +1,4 @@
-// First pass of the two-pass push (a reading of Alg. 1 steps 9-15 that reads V twice per push
+// First pass of the two-pass push (a reading of the CGS2 projections and norm of Alg. 1 that reads V twice per push
 // instead of three times).  Pass B of push j (PASS_B2 in pass.cuh) leaves the new direction
 // pending: w' (w after the first projection) stays in the working vector, s = V^T w' in svec,
 // and h_{j+1,j} comes from ||w' - V s||^2 = ||w'||^2 - ||s||^2.  The next push appends

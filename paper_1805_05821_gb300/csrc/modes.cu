@@ -1,4 +1,4 @@
-// DMD modes Phi_i = V_{1:m} U_r z_i (Alg. 1 step 26): Phi = V Y with Y = [Re y_0, Im y_0, ...]
+// DMD modes Phi_i = V_{1:m} U_r z_i (Alg. 1): Phi = V Y with Y = [Re y_0, Im y_0, ...]
 // (m x ncols, FP64).  SIMT form: each CTA stages 32-row tiles of the row-tiled V in shared
 // memory and every thread accumulates ncols/8 outputs of one row.
 #include <cstdlib>

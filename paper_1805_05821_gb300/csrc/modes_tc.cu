@@ -1,4 +1,4 @@
-// DMD modes on the 5th-generation tensor cores: Phi = V Y (Alg. 1 step 26, Phi_i = V U_r z_i)
+// DMD modes on the 5th-generation tensor cores: Phi = V Y (Alg. 1, Phi_i = V U_r z_i)
 // for FP32 storage, with tcgen05.mma kind::tf32, accumulators in TMEM and a three-term split
 // for FP32-level accuracy:  V Y ~= V_hi Y_hi + V_hi Y_lo + V_lo Y_hi, where x_hi keeps the
 // 19 leading bits of x (a TF32 value) and x_lo = x - x_hi.

@@ -1,11 +1,11 @@
-// Streaming passes over the basis V for one modified-FOA push (Alg. 1 steps 9-15, Alg. 4
-// steps 17-23).  The pass kinds:
+// Streaming passes over the basis V for one modified-FOA push (the pre-vector, the CGS2
+// projections and the norm of Alg. 1; the streaming form of Alg. 4).  The pass kinds:
 //
-//   PASS_A      w = (x - V beta_pre) / beta_jj  (step 9),  h = V^T w         (step 10), ||x||^2
+//   PASS_A      pre-vector w = (x - V beta_pre) / beta_jj,  first projection h = V^T w,  ||x||^2
 //               (QR view: w = x)
-//   PASS_B      w = w - V h                     (step 11), s = V^T w         (step 12)
-//   PASS_C      w = w - V s                     (step 14), ||w||^2           (step 15)
-//   PASS_FIRST  ||x||^2 of the first snapshot (Alg. 1 step 2)
+//   PASS_B      w = w - V h,  reorthogonalisation s = V^T w
+//   PASS_C      w = w - V s,  ||w||^2 (h_{j+1,j} = ||w||)
+//   PASS_FIRST  ||x||^2 of the first snapshot (beta_11 = ||psi_1||)
 //   PASS_B2     pass B of the two-pass push, plus ||w||^2 and the commit of h_{j+1,j} from
 //               ||w - V s||^2 = ||w||^2 - ||s||^2; the new column stays pending (lag.cuh)
 //
@@ -98,7 +98,7 @@ __device__ __forceinline__ void pass_epilogue(const PassArgs &a, DevState *st, d
   } else if constexpr (MODE == PASS_B) {
     for (int c = tid; c < j; c += kConsumers) {
       a.svec[c] = dot[c];
-      a.hvec[c] = a.hvec[c] + dot[c];  // step 13: h = h + s
+      a.hvec[c] = a.hvec[c] + dot[c];  // h = h + s
     }
   } else if constexpr (MODE == PASS_C) {
     if (a.form) {
@@ -154,7 +154,7 @@ __device__ __forceinline__ void pass_epilogue(const PassArgs &a, DevState *st, d
       for (int c = tid; c < j; c += kConsumers) a.H[c + int64_t(j - 1) * ld] = a.hvec[c];
     }
     if (status == FOA_DMD_OK) {
-      // steps 16-18: beta_{i,j+1} = beta_pre_i + h_{i,j} beta_{j,j}; beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}
+      // beta column: beta_{i,j+1} = beta_pre_i + h_{i,j} beta_{j,j}; beta_{j+1,j+1} = h_{j+1,j} beta_{j,j}
       for (int c = tid; c < j; c += kConsumers) a.B[c + int64_t(j) * ld] = a.pre[c] + a.hvec[c] * bjj;
     }
     named_bar_sync(1, kConsumers);
@@ -181,7 +181,7 @@ __device__ __forceinline__ void pass_epilogue(const PassArgs &a, DevState *st, d
       if (a.info_out) *a.info_out = inf;
     }
   } else if constexpr (MODE == PASS_B2) {
-    // steps 12-13 as in PASS_B, then step 15 without a third pass: w still holds w' (after the
+    // s = V^T w' and h += s as in PASS_B, then h_{j+1,j} without a third pass: w still holds w' (after the
     // first projection) and s = V^T w', so ||w' - V s||^2 = ||w'||^2 - ||s||^2 for orthonormal V.
     double *ssq = nrm;  // per-thread partial sums of s_c^2, in column order within a thread
     double t = 0.0;
@@ -247,7 +247,7 @@ __device__ __forceinline__ void pass_epilogue(const PassArgs &a, DevState *st, d
       else if (!(b > 0.0)) status = FOA_DMD_EBREAKDOWN;
       else status = FOA_DMD_OK;
       if (status == FOA_DMD_OK) {
-        a.B[0] = b;  // Alg. 1 step 3
+        a.B[0] = b;  // beta_11 = ||psi_1||
         st->nu = b;
         st->inv_nu = 1.0 / b;
         st->q = 1;

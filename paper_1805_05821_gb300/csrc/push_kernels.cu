@@ -1,5 +1,5 @@
-// Small kernels around the streaming passes: the beta_pre column (Alg. 1 steps 5-8), the
-// append of the new basis vector (step 15) and the gather of basis columns to a dense layout.
+// Small kernels around the streaming passes: the beta_pre column of Alg. 1, the
+// append of the new basis vector v_{j+1} = w / h_{j+1,j} and the gather of basis columns to a dense layout.
 #include "internal.cuh"
 #include "push_kernels.cuh"
 
@@ -24,7 +24,7 @@ int pass_nc_for(int jcap) {
   return need <= 8 ? 8 : need <= 16 ? 16 : need <= 32 ? 32 : need <= 48 ? 48 : 64;
 }
 
-// Decide whether the push proceeds and compute beta_pre (Alg. 1 steps 5-8):
+// Decide whether the push proceeds and compute beta_pre (Alg. 1):
 //   beta_pre_1 = sum_{l=1}^{j-1} h_{1,l} beta_{l,j},  beta_pre_i = sum_{l=i-1}^{j-1} h_{i,l} beta_{l,j}
 // One warp per entry i; lanes split l, FP64 warp reduction.
 __global__ void prep_kernel(DevState *st, const double *H, const double *B, double *pre, int kmax, int first,

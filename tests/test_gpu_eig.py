@@ -1,4 +1,4 @@
-"""GPU parity of the eigen path (Alg. 1 steps 20-29; Secs. 3.2.2-3.2.4) against the oracle.
+"""GPU parity of the eigen path (the eigen extraction of Alg. 1; Secs. 3.2.2-3.2.4) against the oracle.
 
 Eigenvalues are matched by optimal assignment (several orders are equally valid when |c| ties).
 Tolerance for eigenvalue i: 1e-10 ||H||_2 / s_i with s_i = |y_i^H z_i| the condition of the
@@ -284,7 +284,7 @@ def eigvec_tolerance(res_o, scale=1e-10):
 @pytest.mark.parametrize("rank_tol,r_expect", [(0.0, 383), (1e-10, 383), (1e-6, 96)])
 def test_eig_full_size_branches(fields383, rank_tol, r_expect):
     """m = 383: eigenvalues (condition-scaled), indicators, amplitudes and vectors U_r z_i against
-    the oracle (Alg. 1 steps 20-29; Sec. 3.2.3, Eq. errordmdvec; Sec. 3.2.4, Eqs. exrecon/exreconwrt)."""
+    the oracle (the eigen extraction of Alg. 1; Sec. 3.2.3, Eq. errordmdvec; Sec. 3.2.4, Eqs. exrecon/exreconwrt)."""
     spec, g, o = fields383
     rg = g.eig(rank_tol, vec_cols=383)
     ro = o.eig(rank_tol)

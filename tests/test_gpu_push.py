@@ -1,4 +1,4 @@
-"""GPU parity of the streaming push (Alg. 1 steps 2-18, Alg. 4) against the FP64 oracle.
+"""GPU parity of the streaming push (the modified FOA update of Alg. 1, Alg. 4) against the FP64 oracle.
 
 Every case runs the CUDA path through the C ABI and the oracle on the same (storage-rounded)
 inputs.  Tolerances: FP64 storage 1e-10 normwise on beta and H-bar; FP32/BF16 storage column by
@@ -206,8 +206,9 @@ def test_device_generator_matches_host_rows():
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_waves_2d_full_size(dt):
     """1024 x 1024 grid (n = 2^20), N = 200, 20 damped waves, noise 1e-6 relative (kappa_2 = 1.8e6).
-    FP64: state within 1e-10.  FP32: u_s kappa_2(X) is far above 1e-2, so the state is not
-    comparable column by column; the truncated eig (automatic rank) is, through the 20 leading
+    FP64: state within the FP64 law.  FP32: u_s kappa_2(X) is far above 1e-2 (the default FP32
+    breakdown test stops both sides at push 44), so the state is not comparable column by column;
+    the eig truncated at rank_tol = 1e-4 (retained kappa_2 <= 1e4) is, through the 20 leading
     eigenvalues (compare_eigs)."""
     spec = synth.config2(0)
     X = synth.snapshots(spec)
@@ -218,9 +219,8 @@ def test_waves_2d_full_size(dt):
     if dt == "f64":
         compare_state(g, o, dt)
         return
-    import oracle as orc
-    rg = g.eig(rank_tol=-1.0)
-    ro = o.eig(orc.auto_rank_tol(dt, o.m + 1))
+    rg = g.eig(rank_tol=1e-4)
+    ro = o.eig(1e-4)
     assert rg["status"] == 0
     compare_eigs(rg, ro, dt, 20, label="waves 1024^2")
 

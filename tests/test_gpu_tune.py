@@ -1,5 +1,5 @@
 """The launch-geometry autotuner: it times candidates on the handle's own buffers, leaves the
-stream empty, and the pushes that follow still match the oracle (Alg. 1 steps 5-18)."""
+stream empty, and the pushes that follow still match the oracle (the modified FOA update of Alg. 1)."""
 import numpy as np
 import pytest
 

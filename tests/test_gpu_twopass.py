@@ -2,7 +2,7 @@
 
 The two-pass push takes h_{j+1,j} from ||w'||^2 - ||s||^2 (w' after the first projection,
 s = V^T w') and writes v_{j+1} while the next push streams V.  The oracle runs the same reading
-(reorth = 2); in exact arithmetic both equal the CGS2 step of Alg. 1 steps 10-15, so the FP64
+(reorth = 2); in exact arithmetic both equal the CGS2 projections and norm of Alg. 1, so the FP64
 case is also checked against the oracle's three-pass CGS2.  Tolerances as in test_gpu_push:
 FP64 1e-10 normwise, FP32/BF16 column by column within C u_s kappa_2(X_{1:p}) <= 1e-2 (gpu_util).
 """

@@ -35,7 +35,7 @@ def run_oracle(X, k_max=None, tol=None, library=None, reorth=1, form="foa"):
 # ------------------------------------------------------------------ closed forms
 def test_two_snapshot_closed_form():
     """N = 2 (Alg. 1 with one step): h11 = <p1,p2>/|p1|^2, h21 = |p2 - h11 p1|/|p1|,
-    beta12 = <p1,p2>/|p1|, beta22 = |p2 - h11 p1| (derived by hand from steps 2-18)."""
+    beta12 = <p1,p2>/|p1|, beta22 = |p2 - h11 p1| (derived by hand from the update of Alg. 1)."""
     rng = np.random.default_rng(7)
     p1, p2 = rng.standard_normal(1000), rng.standard_normal(1000)
     o = run_oracle(np.stack([p1, p2], axis=1))
@@ -52,7 +52,7 @@ def test_two_snapshot_closed_form():
 
 
 def test_single_snapshot_and_zero_snapshot():
-    """Alg. 1 steps 2-3: beta11 = |psi1|, v1 = psi1/|psi1|; a zero snapshot cannot start a basis."""
+    """First snapshot of Alg. 1: beta11 = |psi1|, v1 = psi1/|psi1|; a zero snapshot cannot start a basis."""
     x = np.arange(1.0, 11.0)
     o = oracle.FoaOracle(10, 4)
     st, h, xn = o.push(x)
