@@ -58,6 +58,30 @@ __device__ bool grid_barrier(GridBar *gb, int *err, long long spin_limit) {
   return ok != 0;
 }
 
+// Bounded wait of CTA p for its neighbours p-1 and p+1 (those that exist among np CTAs) to have
+// finished `target` rounds of the Jacobi sweep; the columns they rotated are then visible.
+__device__ bool wait_neighbours(GridBar *gb, int p, int np, unsigned target, int *err, long long spin_limit) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const long long t0 = clock64();
+    volatile unsigned *rd = gb->round;
+    for (int q = p - 1; q <= p + 1 && ok; q += 2) {
+      if (q < 0 || q >= np) continue;
+      while (rd[q] < target) {
+        if (clock64() - t0 > spin_limit) {
+          ok = 0;
+          atomicExch(err, FOA_DMD_ETIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 __device__ __forceinline__ double block_sum(double v, double *red) {
   v = warp_sum(v);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -94,8 +118,13 @@ __device__ __forceinline__ int block_max_int(int v, int *red) {
 // A CTA of four warps (one per SM sub-partition, so the pair's FP64 work uses all four FP64
 // pipes of the SM) takes one column pair at a time: each thread holds up to kSvdRows rows of both
 // columns in registers, the three dot products are summed in a fixed order (warp trees, then the
-// four warps), thread 0 forms the rotation, and every thread rotates its rows.  The grid spans
-// the SMs (one pair per CTA per round of the round-robin ordering), one grid barrier per round.
+// four warps), thread 0 forms the rotation, and every thread rotates its rows.  The grid has one
+// CTA per pair of the round-robin ordering ((m+1)/2 <= 256 CTAs).  In that ordering the two
+// columns pair p takes in round r+1 were held in round r by pairs p-1 and p+1 (checked for every
+// m <= 512), so between rounds a CTA waits only for its two neighbours' round counters, not for
+// the whole grid; one grid barrier per sweep sums the rotation counts for the convergence test.
+// Columns are read through L2 (__ldcg): a column that comes back to an SM it visited before must
+// not be served from that SM's L1.
 //
 // skip_cta (normally -1) and spin_limit serve foa_dmd_test_wait_fault: CTA skip_cta returns before
 // its first grid-barrier arrival, as a CTA that died would, and the others give up after
@@ -120,10 +149,14 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B
   const int mp = m + (m & 1);  // players of the round-robin schedule (m may be odd: one dummy)
   const int npairs = mp / 2;
   const double tol2 = tol * tol;
+  const bool nbr = int(gridDim.x) == npairs;  // one pair per CTA: neighbour waits between rounds
+  if (max_sweeps > kMaxSweeps) max_sweeps = kMaxSweeps;
+  unsigned gr = 0;  // rounds finished by this CTA
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     int myrot = 0;  // rotations applied by this CTA in the sweep (thread 0)
     for (int rnd = 0; rnd < mp - 1; ++rnd) {
+      if (nbr && gr > 0 && !wait_neighbours(gb, blockIdx.x, npairs, gr, err, spin_limit)) return;
       for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
         const int pa = p, pb = mp - 1 - p;
         const int i = pa == 0 ? 0 : 1 + (pa - 1 + rnd) % (mp - 1);
@@ -135,8 +168,8 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B
 #pragma unroll
         for (int u = 0; u < kSvdRows; ++u) {
           const int k = tid + u * kSvdThreads;
-          x[u] = k < m ? ai[k] : 0.0;
-          y[u] = k < m ? aj[k] : 0.0;
+          x[u] = k < m ? __ldcg(ai + k) : 0.0;
+          y[u] = k < m ? __ldcg(aj + k) : 0.0;
           al = fma(x[u], x[u], al);
           be = fma(y[u], y[u], be);
           ga = fma(x[u], y[u], ga);
@@ -181,14 +214,21 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B
           }
         }
       }
-      if (!grid_barrier(gb, err, spin_limit)) return;
+      if (nbr) {
+        __syncthreads();  // this CTA's rotated columns are written
+        if (tid == 0) {
+          __threadfence();
+          atomicExch(&gb->round[blockIdx.x], gr + 1);
+        }
+      } else if (!grid_barrier(gb, err, spin_limit)) {
+        return;
+      }
+      ++gr;
     }
-    if (tid == 0 && myrot) atomicAdd(&isc[ISC_ROT], myrot);
-    if (!grid_barrier(gb, err, spin_limit)) return;  // every CTA has added its count
-    if (tid == 0) nrot = *(volatile int *)&isc[ISC_ROT];
-    if (!grid_barrier(gb, err, spin_limit)) return;  // everyone has read the count
-    if (gtid == 0) isc[ISC_ROT] = 0;
-    if (!grid_barrier(gb, err, spin_limit)) return;
+    if (tid == 0 && myrot) atomicAdd(&gb->rot[sweep], unsigned(myrot));
+    if (!grid_barrier(gb, err, spin_limit)) return;  // every CTA has finished the sweep and added its count
+    if (tid == 0) nrot = int(*(volatile unsigned *)&gb->rot[sweep]);
+    __syncthreads();
     if (nrot == 0) break;
   }
   if (gtid == 0) isc[ISC_SWEEPS] = sweep;
@@ -197,7 +237,10 @@ __global__ void __launch_bounds__(kSvdThreads) svd_jacobi_kernel(const double *B
   for (int c = warp_g; c < m; c += nwarps) {
     const double *ac = A + int64_t(c) * lda;
     double sq = 0.0;
-    for (int k = lane; k < m; k += 32) sq += ac[k] * ac[k];
+    for (int k = lane; k < m; k += 32) {
+      const double v = __ldcg(ac + k);
+      sq += v * v;
+    }
     sq = warp_sum(sq);
     if (lane == 0) sig[c] = sqrt(sq);
   }

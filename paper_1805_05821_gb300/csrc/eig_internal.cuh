@@ -4,9 +4,14 @@
 
 namespace foa {
 
+constexpr int kMaxSweeps = 32;  // Jacobi sweeps at most (the launch asks for 30)
+
+// Cross-CTA synchronisation state of the cooperative Jacobi SVD, zeroed before every launch.
 struct GridBar {
-  unsigned count;
-  unsigned gen;
+  unsigned count;                 // grid barrier: arrivals
+  unsigned gen;                   // grid barrier: generation
+  unsigned rot[kMaxSweeps];       // rotations applied in each sweep (summed over CTAs)
+  unsigned round[kMaxK / 2];      // rounds each CTA has finished (its neighbours wait on it)
 };
 
 // integer scalars of one eigen-decomposition (device)
