@@ -214,7 +214,7 @@ def test_projection_error_grows_like_kappa():
     ks, es = np.log10(ks), np.log10(es)
     sel = ks < 14.0
     slope = np.polyfit(ks[sel], es[sel], 1)[0]
-    assert 0.6 <= slope <= 1.4, slope
+    assert 0.8 <= slope <= 1.2, slope  # measured 0.92
     # and the error stays within a modest multiple of eps kappa
     assert np.all(es[sel] <= ks[sel] + np.log10(U64) + 4)
 
@@ -262,11 +262,43 @@ def test_amplitudes_reconstruct_snapshots():
     Phi = o.V[:, :m] @ res["Z"]
     s = np.linalg.svd(X[:, :m], compute_uv=False)
     kappa = s[0] / s[-1]
+    # rounding enters through the projection (u kappa_2(X)), the eigenvector basis (cond(Z)) and
+    # the powers lambda^(k-1); measured errors are 1e-15 ... 6e-15 against bounds near 2e-13, so a
+    # percent-level error in one amplitude fails
+    condz = np.linalg.cond(res["Z"])
+    growth = max(1.0, np.abs(res["lam"]).max())
     for k in range(1, N):
         rec = (Phi * (res["amp"] * res["lam"] ** (k - 1))[None, :]).sum(axis=1)
-        if k <= N - 1:
-            err = np.linalg.norm(rec - X[:, k - 1]) / np.linalg.norm(X[:, k - 1])
-            assert err <= 1e4 * U64 * kappa * 10 ** (0.5 * k), (k, err)
+        err = np.linalg.norm(rec - X[:, k - 1]) / np.linalg.norm(X[:, k - 1])
+        assert err <= 100 * U64 * kappa * condz * growth ** (k - 1), (k, err)
+    # a 1% error in the largest amplitude is caught
+    amp = res["amp"].copy()
+    amp[0] *= 1.01
+    rec = (Phi * amp[None, :]).sum(axis=1)
+    assert np.linalg.norm(rec - X[:, 0]) / np.linalg.norm(X[:, 0]) > 100 * U64 * kappa * condz
+
+
+def test_modes_are_eigenvectors_of_the_known_map():
+    """The planted rank-10 map (exact Krylov case, breakdown at push 11): every DMD mode
+    Phi_i = V U_r z_i (Alg. 1) is a unit eigenvector of A with eigenvalue lambda_i, untruncated
+    and truncated (Sec. 3.2.4: a zero h_{N,N-1} makes the Ritz pairs exact)."""
+    spec = synth.config1(0)
+    X = synth.snapshots(spec)
+    A = synth.planted_map(spec)
+    o = run_oracle(X, 32)
+    assert o.stopped and o.m == 10
+    for rank_tol in (0.0, 1e-12):
+        res = o.eig(rank_tol)
+        Phi = o.modes(res, res["r"])
+        assert Phi.shape == (spec.n, 10)
+        for i in range(10):
+            ph = Phi[:, i]
+            assert abs(np.linalg.norm(ph) - 1.0) <= 1e-12
+            r = np.linalg.norm(A @ ph - res["lam"][i] * ph)
+            assert r <= 1e-9, (rank_tol, i, r)
+        # modes follow the |c| order of the eigenvalues they belong to: a swapped column fails
+        sw = Phi[:, [1, 0]]
+        assert np.linalg.norm(A @ sw[:, 0] - res["lam"][0] * sw[:, 0]) > 1e-3
 
 
 def test_ordering_rule():
