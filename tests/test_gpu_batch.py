@@ -156,3 +156,45 @@ def test_batched_wide_bases(dt):
             compare_columns(q, o.m, H, B, o, dt, V=V, label=f"batched stream {s} n={sp.n}")
     finally:
         F.foa_dmd_batch_destroy(b)
+
+
+def test_batched_statuses_follow_the_oracle():
+    """Per-stream statuses inside one batch (Sec. 3.2.4 and reading 4 of the breakdown test): a
+    noise-free planted rank-6 map breaks down at push 7 and stays stopped while the batch goes on;
+    a snapshot holding a NaN is refused (state unchanged) and the stream continues with the next
+    one; a Gaussian stream is unaffected.  States against the oracle fed the same sequences (the
+    oracle skips the refused snapshot as the batch does)."""
+    import torch
+    from types import SimpleNamespace
+    from paper_1805_05821_gb300 import foa_dmd as F
+    import oracle
+    planted = synth.planted(6000, 12, 6, seed=77, noise_rel=0.0)
+    Xp = synth.snapshots(planted)
+    Xn = np.random.default_rng(78).standard_normal((5000, 12))
+    Xn[123, 4] = np.nan                               # the fifth snapshot of stream 1 is refused
+    Xg = np.random.default_rng(79).standard_normal((7000, 12))
+    specs = [SimpleNamespace(n=6000, N=12), SimpleNamespace(n=5000, N=12), SimpleNamespace(n=7000, N=12)]
+    b, hosts = run_batch(specs, set(), use_graph=True, Xs=[Xp, Xn, Xg])
+    try:
+        # stream 0: breakdown at push 7, q = 6, stopped (status of its last push EBREAKDOWN or ESTOPPED)
+        q, status, H, B = F.foa_dmd_batch_get_state(b, 0, 12)
+        o = oracle.FoaOracle(6000, 12, storage="f32")
+        sts = [o.push(hosts[0][:, t])[0] for t in range(12)]
+        assert sts[:6] == ["ok"] * 6 and sts[6] == "breakdown" and o.q == 6
+        assert q == 6 and status in (F.EBREAKDOWN, F.ESTOPPED), (q, status)
+        assert H[6, 5] == 0.0 and np.any(H[:6, 5] != 0.0)
+        compare_columns(q, o.m, H, B, o, "f32", label="batched breakdown stream")
+        # stream 1: the NaN snapshot is refused, the other 11 are pushed
+        q, status, H, B = F.foa_dmd_batch_get_state(b, 1, 12)
+        o = oracle.FoaOracle(5000, 12, storage="f32")
+        sts = [o.push(hosts[1][:, t])[0] for t in range(12)]
+        assert sts[4] == "nonfinite" and o.q == 11
+        assert q == 11 and status == F.OK, (q, status)
+        compare_columns(q, o.m, H, B, o, "f32", label="batched NaN stream")
+        # stream 2: all 12
+        q, status, H, B = F.foa_dmd_batch_get_state(b, 2, 12)
+        o = oracle_state(hosts[2], 12)
+        assert q == o.q == 12 and status == F.OK
+        compare_columns(q, o.m, H, B, o, "f32", label="batched Gaussian stream")
+    finally:
+        F.foa_dmd_batch_destroy(b)
