@@ -63,16 +63,21 @@ def parse():
                    help="skip the secondary lines: the two-pass push on the same workload, the 256 batched "
                         "streams and the FP64/FP32/BF16 storage forms on the 1024^2 waves")
     p.add_argument("--sample-grid", type=int, default=40, help="grid of the CPU-oracle sample")
-    p.add_argument("--workload", default="fields", choices=["fields", "batched", "forms", "waves3d"],
+    p.add_argument("--workload", default="fields", choices=["fields", "batched", "forms", "waves3d", "blocksweep"],
                    help="fields: the 4-field 256^3 stream (default); batched: 256 uneven planted streams; "
                         "forms: storage forms and the kappa sweep; waves3d: the 256^3 single-field waves "
-                        "(kappa_t 1e4) through the three-pass push and the block push of 4")
+                        "(kappa_t 1e4) through the three-pass push and the block push of 4; blocksweep: the "
+                        "three block passes of one block of 4 at a list of basis sizes")
     p.add_argument("--reps", type=int, default=2, help="waves3d: timed repetitions of each push form")
     p.add_argument("--streams", type=int, default=256)
     p.add_argument("--batch-n", type=int, default=0,
                    help="batched: give every stream this length (planted rank 16, noise 1e-5) instead of the "
                         "log-uniform mix; a small case for profiling")
     p.add_argument("--batch-snapshots", type=int, default=0, help="batched with --batch-n: snapshots per stream")
+    p.add_argument("--block-n", type=int, default=1 << 24, help="blocksweep: rows")
+    p.add_argument("--block-dtype", default="f32", choices=["f32", "bf16"], help="blocksweep: storage type")
+    p.add_argument("--block-j", default="32,64,128,192,256,320,384,448,500",
+                   help="blocksweep: basis sizes (comma separated) at which one block of 4 is pushed")
     return p.parse_args()
 
 
@@ -255,6 +260,8 @@ def main():
         return run_forms(args)
     if args.workload == "waves3d":
         return run_waves3d(args)
+    if args.workload == "blocksweep":
+        return run_block_sweep(args)
     world, rank, local = dist_env()
     import torch
     if world > 1:
@@ -733,6 +740,65 @@ def run_waves3d(args):
         out[label] = {"value": N / (ms / 1e3), "ms": ms, "q": F.foa_dmd_get_state(h, N)[0], "per_kind": kinds}
     F.foa_dmd_destroy(h)
     out["value"] = out["three_pass"]["value"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_block_sweep(args):
+    """Secondary measurement: the block passes A, B and C (foa_dmd_push_block) of one block of 4
+    Gaussian snapshots (seeded, generated on the device) at each basis size j of --block-j, after j
+    single pushes, with --block-n rows and --block-dtype storage.  GB/s per pass kind from the
+    handle's CUDA-event counters (V once plus the block's vectors), best of two."""
+    import ctypes
+    import torch
+    from paper_1805_05821_gb300 import build
+    from paper_1805_05821_gb300 import foa_dmd as F
+    build.build()
+    n, dt = args.block_n, args.block_dtype
+    js = [int(v) for v in args.block_j.split(",")]
+    N = max(js) + 4
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((N, n), generator=gen, device="cuda", dtype=torch.float32)
+    if dt == "bf16":
+        X = X.to(torch.bfloat16)
+    L = F.lib()
+    h = F.foa_dmd_create(n, N, dt, F.foa_dmd_opts_default())
+    peak, _ = measured_peak()
+
+    def singles(j):
+        F.foa_dmd_reset(h)
+        for t in range(j):
+            st = L.foa_dmd_push(h, ctypes.c_void_p(X[t].data_ptr()), None)
+            if st:
+                raise RuntimeError(f"push {t}: {F.STATUS.get(st, st)}")
+        torch.cuda.synchronize()
+
+    rows = {}
+    for j in js:
+        best = None
+        for _ in range(2):
+            singles(j)
+            F.foa_dmd_profile_read(h)
+            F.foa_dmd_profile(h, True)
+            st = L.foa_dmd_push_block(h, ctypes.c_void_p(X[j].data_ptr()), 4, n, 4, None)
+            torch.cuda.synchronize()
+            F.foa_dmd_profile(h, False)
+            stats = F.foa_dmd_profile_read(h)
+            if st:
+                raise RuntimeError(f"block push at j={j}: {F.STATUS.get(st, st)}")
+            us = sum(stats["ms"][:3]) * 1e3
+            if best is None or us < best[0]:
+                best = (us, stats)
+        stats = best[1]
+        rows[j] = {k: {"us": stats["ms"][i] * 1e3, "GBps": stats["bytes"][i] / (stats["ms"][i] / 1e3) / 1e9,
+                       "frac": stats["bytes"][i] / (stats["ms"][i] / 1e3) / 1e9 / peak}
+                   for i, k in enumerate("ABC")}
+    F.foa_dmd_destroy(h)
+    out = {"metric": "GB/s of the block passes (one block of 4)", "unit": "GB/s", "data": "synthetic",
+           "dtype": dt, "higher_is_better": True, "peak_GBps": peak,
+           "config": {"workload": f"blocksweep n={n} Gaussian snapshots, {dt} storage, block of 4 at j in {js}",
+                      "timing": "CUDA events of the handle's pass counters, best of 2"},
+           "per_j": rows}
     print(json.dumps(out), flush=True)
     return 0
 

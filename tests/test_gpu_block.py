@@ -163,8 +163,9 @@ def test_block_push_stops_at_its_resolution_limit_on_fields():
 
 @pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4)])
 def test_block_push_widest_basis(dt, block):
-    """n = 4097 Gaussian snapshots (ragged last tile), N = 421 = 1 + 105 blocks of 4: the column
-    sweep's threads take up to eight columns each (j > 384) and every column-count instance runs."""
+    """n = 4097 Gaussian snapshots (ragged last tile), N = 421 = 1 + 105 blocks of 4: the block
+    passes run in every shape (256-thread CTAs with two, four or eight columns a thread up to
+    j = 256, one 512-thread CTA per SM with eight columns a thread beyond)."""
     import torch
     from paper_1805_05821_gb300.foa_dmd import FoaDMD
     n, N = 4097, 421
