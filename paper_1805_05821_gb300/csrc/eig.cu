@@ -385,38 +385,53 @@ __global__ void hessenberg_kernel(double *G, int ldg, double *Q, int ldq, const 
 // subdiagonal search, the exceptional shifts after 10 and 20 iterations without deflation
 // (0.75 s and -0.4375 s^2), the search for two small consecutive subdiagonals and the bulge-
 // chasing sweep with its p, q, r, x, y, z, w quantities (Golub & Van Loan, Sec. 7.5, give the
-// same method).  Here the row and column updates of every sweep step are spread over the CTA.
-// Works in place on a copy A.  A conjugate pair is stored +Im first.
+// same method).  Works in place on a copy A.  A conjugate pair is stored +Im first.
+//
+// Layout: the band |j - i| <= 3 (every entry the bulge chase reads, 7 n doubles) lives in shared
+// memory; the rest of A in shared memory when n^2 fits the smem_elems doubles offered, else in
+// global memory.  Sweep step k applies reflector k to rows k..k+2 (columns k..nn) and then to
+// columns k..k+2 (rows l..k+3).  Warp 0 takes the corner, rows/columns k..k+3 (all band
+// entries): lanes 0-3 the row update of columns k..k+3, then the column update of rows k..k+3,
+// and lane 0 forms reflector k+1 from column k; the other warps apply reflector k to rows k..k+2
+// of columns k+4..nn and to columns k..k+2 of rows l..k-1, a fixed thread per column and per
+// row.  Those entries are never read by the chase within the sweep, so one CTA barrier per step
+// suffices, and every entry receives the same updates in the same order as the sequential sweep.
 __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, double *wi, int *isc,
                            int smem_elems) {
   const int n = isc_in[ISC_R];
   extern __shared__ double sh[];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int T1 = blockDim.x - 32;  // threads outside warp 0
   double *a = Ag;
   int ld = lda;
-  // The order n is known only here (the truncated rank r is counted on the device): the matrix is
-  // copied into the dynamic shared memory whenever it fits the smem_elems doubles provided.
+  double *band = sh + smem_elems;  // entry (i, j), |j - i| <= 3, at band[7 i + j - i + 3]
   if (int64_t(n) * n <= int64_t(smem_elems)) {
     a = sh;
     ld = n;
-    for (int64_t e = threadIdx.x; e < int64_t(n) * n; e += blockDim.x) {
+    for (int64_t e = tid; e < int64_t(n) * n; e += blockDim.x) {
       const int i = int(e % n), c = int(e / n);
       a[i + int64_t(c) * n] = Ag[i + int64_t(c) * lda];
     }
   }
-#define AA(i, j) a[(i) + int64_t(j) * ld]
+  for (int e = tid; e < 7 * n; e += blockDim.x) {
+    const int i = e / 7, j = i + e % 7 - 3;
+    band[e] = (j >= 0 && j < n) ? Ag[i + int64_t(j) * lda] : 0.0;
+  }
+#define AA(i, j) (*((((j) - (i)) <= 3 && ((i) - (j)) <= 3) ? &band[7 * (i) + (j) - (i) + 3] : &a[(i) + int64_t(j) * ld]))
   __shared__ double red[32];
   __shared__ int ired[32];
-  __shared__ double sp, sq, sr, sx, sy, sz, st_, sw, sanorm;
+  __shared__ double sp, sq, sx, st_, sw, sanorm;
   __shared__ int snn, sits, sskip, sfail;
-  __shared__ double fwd[3];  // column k, rows k+1..k+3, after step k of a sweep
+  __shared__ double rfl[2][5];  // reflector of step k in slot k & 1: x, y, z, q, r
+  __shared__ int rskip[2];
   __syncthreads();
   double an = 0.0;
-  for (int64_t e = threadIdx.x; e < int64_t(n) * n; e += blockDim.x) {
+  for (int64_t e = tid; e < int64_t(n) * n; e += blockDim.x) {
     const int i = int(e % n), c = int(e / n);
     if (i <= c + 1) an += fabs(AA(i, c));
   }
   an = block_sum(an, red);
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     sanorm = an;
     snn = n - 1;
     st_ = 0.0;
@@ -425,21 +440,72 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
   }
   __syncthreads();
   const double eps = 2.220446049250313e-16;
+  // Reflector of step k from (p, q, r) (the first step m gets them already scaled); records it in
+  // slot k & 1 and writes A(k, k-1).  Lane 0 of warp 0 only.  Past the first step (p, q, r) are
+  // scaled by the power of two x nearest below max(|p|, |q|, |r|), which is exact: on GB300 a
+  // dependent FP64 operation takes about 64 cycles and a division about 420, and the reflector is
+  // the chase's critical path, so the division by |p| + |q| + |r| of the sequential routine is
+  // replaced; the reflector (p/s, q/s, r/s, q/p, r/p) does not depend on the scale.
+  auto reflector = [&](int k, int m, int l, double p, double q, double r, double x) {
+    bool go = true;
+    if (k != m) {
+      const double mx = fmax(fabs(p), fmax(fabs(q), fabs(r)));
+      const long long eb = (__double_as_longlong(mx) >> 52) & 0x7ff;  // biased exponent of mx
+      if (mx != 0.0 && eb != 0 && eb < 2046) {
+        x = __longlong_as_double(eb << 52);                        // 2^(e), e the exponent of mx
+        const double ix = __longlong_as_double((2046 - eb) << 52);  // 2^(-e)
+        p *= ix;
+        q *= ix;
+        r *= ix;
+      } else if (mx != 0.0) {  // subnormal or near-overflow maximum: the division as in hqr
+        x = fabs(p) + fabs(q) + fabs(r);
+        const double ix = 1.0 / x;
+        p *= ix;
+        q *= ix;
+        r *= ix;
+      } else {
+        go = false;
+      }
+    }
+    double s = 0.0;
+    if (go) {
+      s = copysign(sqrt(p * p + q * q + r * r), p);
+      if (s == 0.0) go = false;
+    }
+    const int b = k & 1;
+    if (go) {
+      if (k == m) {
+        if (l != m) AA(k, k - 1) = -AA(k, k - 1);
+      } else {
+        AA(k, k - 1) = -s * x;
+      }
+      p += s;
+      const double is = 1.0 / s, ip = 1.0 / p;
+      rfl[b][0] = p * is;
+      rfl[b][1] = q * is;
+      rfl[b][2] = r * is;
+      rfl[b][3] = q * ip;
+      rfl[b][4] = r * ip;
+      rskip[b] = 0;
+    } else {
+      rskip[b] = 1;
+    }
+  };
   while (true) {
     const int nn = snn;
     if (nn < 0 || sfail) break;
     // largest l in [1, nn] whose subdiagonal is negligible (0 if none)
     int cand = 0;
-    for (int l = 1 + threadIdx.x; l <= nn; l += blockDim.x) {
+    for (int l = 1 + tid; l <= nn; l += blockDim.x) {
       double s = fabs(AA(l - 1, l - 1)) + fabs(AA(l, l));
       if (s == 0.0) s = sanorm;
       if (fabs(AA(l, l - 1)) <= eps * s) cand = max(cand, l);
     }
     const int l = block_max_int(cand, ired);
-    if (threadIdx.x == 0 && l > 0) AA(l, l - 1) = 0.0;
+    if (tid == 0 && l > 0) AA(l, l - 1) = 0.0;
     __syncthreads();
     if (l == nn) {
-      if (threadIdx.x == 0) {
+      if (tid == 0) {
         wr[nn] = AA(nn, nn) + st_;
         wi[nn] = 0.0;
         snn = nn - 1;
@@ -449,7 +515,7 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
       continue;
     }
     if (l == nn - 1) {
-      if (threadIdx.x == 0) {
+      if (tid == 0) {
         const double y = AA(nn - 1, nn - 1), x = AA(nn, nn) + st_;
         const double w = AA(nn, nn - 1) * AA(nn - 1, nn);
         const double p = 0.5 * (y - AA(nn, nn));
@@ -472,12 +538,12 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
       continue;
     }
     if (sits >= 60) {
-      if (threadIdx.x == 0) sfail = 1;
+      if (tid == 0) sfail = 1;
       __syncthreads();
       break;
     }
     // shifts
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double x = AA(nn, nn), y = AA(nn - 1, nn - 1), w = AA(nn, nn - 1) * AA(nn - 1, nn);
       if (sits == 10 || sits == 20) {
         st_ += x;
@@ -497,13 +563,13 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
     __syncthreads();
     if (sskip) {
       const double xs = sx;
-      for (int i = threadIdx.x; i <= nn; i += blockDim.x) AA(i, i) -= xs;
+      for (int i = tid; i <= nn; i += blockDim.x) AA(i, i) -= xs;
       __syncthreads();
     }
     const double X = sp, Y = sq, W = sw;
     // largest m in [l, nn-2] where two consecutive subdiagonals are small (or m = l)
     int mc = l;
-    for (int m = l + 1 + threadIdx.x; m <= nn - 2; m += blockDim.x) {
+    for (int m = l + 1 + tid; m <= nn - 2; m += blockDim.x) {
       const double z = AA(m, m);
       const double r = X - z, s = Y - z;
       double p = (r * s - W) / AA(m + 1, m) + AA(m, m + 1);
@@ -518,100 +584,114 @@ __global__ void hqr_kernel(double *Ag, int lda, const int *isc_in, double *wr, d
       if (u <= eps * v) mc = max(mc, m);
     }
     const int m = block_max_int(mc, ired);
-    if (threadIdx.x == 0) {
+    for (int i = m + 2 + tid; i <= nn; i += blockDim.x) {
+      AA(i, i - 2) = 0.0;
+      if (i != m + 2) AA(i, i - 3) = 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
       const double z = AA(m, m);
       const double r = X - z, s = Y - z;
       double p = (r * s - W) / AA(m + 1, m) + AA(m, m + 1);
       double q = AA(m + 1, m + 1) - z - r - s;
       double rr = AA(m + 2, m + 1);
       const double sc = fabs(p) + fabs(q) + fabs(rr);
-      sp = p / sc;
-      sq = q / sc;
-      sr = rr / sc;
-    }
-    for (int i = m + 2 + threadIdx.x; i <= nn; i += blockDim.x) {
-      AA(i, i - 2) = 0.0;
-      if (i != m + 2) AA(i, i - 3) = 0.0;
+      reflector(m, m, l, p / sc, q / sc, rr / sc, 0.0);
     }
     __syncthreads();
-    // double-shift QR sweep on rows/columns l..nn, starting at m.  The column update of step k
-    // produces column k's entries of rows k+1..k+3, which step k+1 reflects: the threads that
-    // compute them pass them on through shared memory (fwd) instead of a re-read.
+    // double-shift QR sweep on rows/columns l..nn, starting at m; one barrier per step
     for (int k = m; k <= nn - 1; ++k) {
-      if (threadIdx.x == 0) {
-        double p = sp, q = sq, r = sr, x = 0.0;
-        bool go = true;
-        if (k != m) {
-          p = fwd[0];
-          q = fwd[1];
-          r = (k != nn - 1) ? fwd[2] : 0.0;
-          x = fabs(p) + fabs(q) + fabs(r);
-          if (x != 0.0) {
-            const double ix = 1.0 / x;
-            p *= ix;
-            q *= ix;
-            r *= ix;
-          } else {
-            go = false;
+      const int b = k & 1;
+      const bool three = (k != nn - 1);
+      const bool skip = rskip[b] != 0;
+      const double x = rfl[b][0], y = rfl[b][1], z = rfl[b][2], q = rfl[b][3], r = rfl[b][4];
+      if (tid < 32) {
+        // ---- warp 0: the corner, then the next reflector
+        double fw = 0.0;  // lane 1 + i: row k + 1 + i of column k after the step
+        if (!skip) {
+          const int jj = k + lane;
+          if (lane < 4 && jj <= nn) {
+            double p = AA(k, jj) + q * AA(k + 1, jj);
+            if (three) {
+              p += r * AA(k + 2, jj);
+              AA(k + 2, jj) -= p * z;
+            }
+            AA(k + 1, jj) -= p * y;
+            AA(k, jj) -= p * x;
           }
-        }
-        double s = 0.0;
-        if (go) {
-          s = copysign(sqrt(p * p + q * q + r * r), p);
-          if (s == 0.0) go = false;
-        }
-        if (go) {
-          if (k == m) {
-            if (l != m) AA(k, k - 1) = -AA(k, k - 1);
-          } else {
-            AA(k, k - 1) = -s * x;
+          __syncwarp();
+          const int i = k + lane;
+          if (lane < 4 && i <= nn && i <= k + 3) {
+            double p = x * AA(i, k) + y * AA(i, k + 1);
+            if (three) {
+              p += z * AA(i, k + 2);
+              AA(i, k + 2) -= p * r;
+            }
+            AA(i, k + 1) -= p * q;
+            const double aik = AA(i, k) - p;
+            AA(i, k) = aik;
+            fw = aik;
           }
-          p += s;
-          const double is = 1.0 / s, ip = 1.0 / p;
-          sx = p * is;
-          sy = q * is;
-          sz = r * is;
-          sq = q * ip;
-          sr = r * ip;
-          sskip = 0;
         } else {
-          sskip = 1;
+          const int i = k + lane;
+          if (lane >= 1 && lane < 4 && i <= nn) fw = AA(i, k);
         }
-      }
-      __syncthreads();
-      if (!sskip) {
-        const double x = sx, y = sy, z = sz, q = sq, r = sr;
-        const bool three = (k != nn - 1);
-        for (int jj = k + threadIdx.x; jj <= nn; jj += blockDim.x) {
-          double p = AA(k, jj) + q * AA(k + 1, jj);
+        const double f0 = __shfl_sync(0xffffffffu, fw, 1);
+        const double f1 = __shfl_sync(0xffffffffu, fw, 2);
+        const double f2 = __shfl_sync(0xffffffffu, fw, 3);
+        if (lane == 0 && k + 1 <= nn - 1) reflector(k + 1, m, l, f0, f1, (k + 1 != nn - 1) ? f2 : 0.0, 0.0);
+      } else if (!skip) {
+        // ---- the other warps: columns k+4..nn (rows k..k+2) and rows l..k-1 (columns k..k+2),
+        // at most two of each a thread (n <= 512 < 2 T1); every load issued before any update,
+        // so the step waits for one memory round trip
+        const int t1 = tid - 32;
+        const int j0 = k + 4 + ((t1 - (k + 4)) % T1 + T1) % T1, j1 = j0 + T1;
+        const int i0 = l + ((t1 - l) % T1 + T1) % T1, i1 = i0 + T1;
+        const bool hj0 = j0 <= nn, hj1 = j1 <= nn, hi0 = i0 <= k - 1, hi1 = i1 <= k - 1;
+        double c0[3] = {0.0, 0.0, 0.0}, c1[3] = {0.0, 0.0, 0.0}, r0[3] = {0.0, 0.0, 0.0}, r1[3] = {0.0, 0.0, 0.0};
+        if (hj0) {
+          c0[0] = AA(k, j0), c0[1] = AA(k + 1, j0);
+          if (three) c0[2] = AA(k + 2, j0);
+        }
+        if (hj1) {
+          c1[0] = AA(k, j1), c1[1] = AA(k + 1, j1);
+          if (three) c1[2] = AA(k + 2, j1);
+        }
+        if (hi0) {
+          r0[0] = AA(i0, k), r0[1] = AA(i0, k + 1);
+          if (three) r0[2] = AA(i0, k + 2);
+        }
+        if (hi1) {
+          r1[0] = AA(i1, k), r1[1] = AA(i1, k + 1);
+          if (three) r1[2] = AA(i1, k + 2);
+        }
+        auto rowupd = [&](double (&v)[3], int jj) {
+          double p = v[0] + q * v[1];
           if (three) {
-            p += r * AA(k + 2, jj);
-            AA(k + 2, jj) -= p * z;
+            p += r * v[2];
+            AA(k + 2, jj) = v[2] - p * z;
           }
-          AA(k + 1, jj) -= p * y;
-          AA(k, jj) -= p * x;
-        }
-        __syncthreads();
-        const int mmin = nn < k + 3 ? nn : k + 3;
-        for (int i = l + threadIdx.x; i <= mmin; i += blockDim.x) {
-          double p = x * AA(i, k) + y * AA(i, k + 1);
+          AA(k + 1, jj) = v[1] - p * y;
+          AA(k, jj) = v[0] - p * x;
+        };
+        auto colupd = [&](double (&v)[3], int i) {
+          double p = x * v[0] + y * v[1];
           if (three) {
-            p += z * AA(i, k + 2);
-            AA(i, k + 2) -= p * r;
+            p += z * v[2];
+            AA(i, k + 2) = v[2] - p * r;
           }
-          AA(i, k + 1) -= p * q;
-          const double aik = AA(i, k) - p;
-          AA(i, k) = aik;
-          if (i > k) fwd[i - k - 1] = aik;
-        }
-      } else {
-        // no reflection: the next step reads column k as it stands
-        for (int i = k + 1 + threadIdx.x; i <= k + 3 && i <= nn; i += blockDim.x) fwd[i - k - 1] = AA(i, k);
+          AA(i, k + 1) = v[1] - p * q;
+          AA(i, k) = v[0] - p;
+        };
+        if (hj0) rowupd(c0, j0);
+        if (hj1) rowupd(c1, j1);
+        if (hi0) colupd(r0, i0);
+        if (hi1) colupd(r1, i1);
       }
       __syncthreads();
     }
   }
-  if (threadIdx.x == 0) isc[ISC_STATUS] = sfail ? FOA_DMD_ENOCONV : FOA_DMD_OK;
+  if (tid == 0) isc[ISC_STATUS] = sfail ? FOA_DMD_ENOCONV : FOA_DMD_OK;
 #undef AA
 }
 

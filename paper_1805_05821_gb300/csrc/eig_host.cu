@@ -134,14 +134,18 @@ static int enqueue_eig(foa_dmd *h, EigWork *w, cudaStream_t s, int m, double ran
   e = cudaMemcpyAsync(w->Aqr, w->G, size_t(K) * K * 8, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
   // The QR iteration works on the r x r matrix (r = m without truncation); r is counted on the
-  // device, so the launch offers min(m^2, 160^2) doubles of shared memory and the kernel copies the
-  // matrix there when r^2 fits (every truncated eig with r <= 160, whatever m).
-  const size_t qr_smem = std::min(size_t(m) * m, size_t(kQrSmemMaxOrder) * kQrSmemMaxOrder) * 8;
+  // device.  The launch offers the band |j - i| <= 3 (7 m doubles) and up to 160^2 doubles for the
+  // whole matrix, which the kernel copies to shared memory when r^2 fits (every truncated eig with
+  // r <= 160, whatever m).
+  const size_t band = 7 * size_t(m);
+  const size_t full = std::min(std::min(size_t(m) * m, size_t(kQrSmemMaxOrder) * kQrSmemMaxOrder),
+                               size_t(232448 / 8) - band - 512);  // 4 KB left for the static variables
+  const size_t qr_smem = (full + band) * 8;
   if (qr_smem > 48 * 1024) {
     e = cudaFuncSetAttribute(hqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(qr_smem));
     if (e != cudaSuccess) return cuda_status(e);
   }
-  hqr_kernel<<<1, 512, qr_smem, s>>>(w->Aqr, K, w->isc, w->wr, w->wi, w->isc, int(qr_smem / 8));
+  hqr_kernel<<<1, 512, qr_smem, s>>>(w->Aqr, K, w->isc, w->wr, w->wi, w->isc, int(full));
   EigArgs a;
   memset(&a, 0, sizeof(a));
   a.Hs = w->G;
