@@ -487,7 +487,51 @@ MUTANTS = {
     "qr_beta_diag": ("    BT(j, j) = nu;\n", "    BT(j, j) = nu * bjj;\n"),
     "qr_hbar_index": ("acc += HB(i, l) * BT(l, jc);\n    HB(i, jc) = (h[i] - acc) / bjj;",
                       "acc += HB(i, l) * BT(jc, l);\n    HB(i, jc) = (h[i] - acc) / bjj;"),
+    "drop_h_plus_s": ("    /* reorthogonalisation */\n    gemv_t(n, j, V, ldv, w, s, part);\n"
+                      "    for (int32_t i = 0; i < j; ++i) h[i] = h[i] + s[i];",
+                      "    /* reorthogonalisation */\n    gemv_t(n, j, V, ldv, w, s, part);\n"
+                      "    for (int32_t i = 0; i < j; ++i) h[i] = h[i];"),
+    "qr_drop_h_plus_s": ("w[r] = x[r] - y[r];\n  if (reorth) {\n    gemv_t(n, j, V, ldv, w, s, part);\n"
+                         "    for (int32_t i = 0; i < j; ++i) h[i] = h[i] + s[i];",
+                         "w[r] = x[r] - y[r];\n  if (reorth) {\n    gemv_t(n, j, V, ldv, w, s, part);\n"
+                         "    for (int32_t i = 0; i < j; ++i) h[i] = h[i];"),
 }
+
+
+def _step_from_perturbed_basis(library, form, delta=1e-6, n=60, j=8):
+    """One push from a basis whose orthogonality is off by delta.  The CGS2 steps give
+    psi = V beta_{:,j+1} (the QR view of Sec. 3.1: X = V beta, with the pre-vector of Alg. 1 in the
+    FOA form) as an algebraic identity whatever V's orthogonality, because the second projection's
+    coefficients s are added to h; without that sum the residual is beta_jj V s, of order delta.
+    Returns the relative residual of psi - V beta_{:,j+1}."""
+    rng = np.random.default_rng(17)
+    k = j + 2
+    Q, _ = np.linalg.qr(rng.standard_normal((n, j)))
+    V = np.zeros((n, k), order="F")
+    V[:, :j] = Q + delta * rng.standard_normal((n, j))
+    H = np.zeros((k, k), order="F")
+    B = np.zeros((k, k), order="F")
+    B[:j, :j] = np.triu(rng.standard_normal((j, j)))
+    B[np.arange(j), np.arange(j)] = 1.0 + rng.random(j)
+    H[:j, :j - 1] = np.triu(rng.standard_normal((j, j - 1)), -1)
+    x = rng.standard_normal(n)
+    out = np.zeros(2)
+    step = library.foa_oracle_qr_step if form == "qr" else library.foa_oracle_step
+    st = step(n, j, oracle._ptr(V), n, oracle._ptr(H), k, oracle._ptr(B), k, oracle._ptr(x), 1e-300, 1,
+              oracle._ptr(out))
+    assert st == 0
+    res = x - V[:, :j + 1] @ B[:j + 1, j]
+    return np.linalg.norm(res) / np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("form", ["foa", "qr"])
+def test_cgs2_identity_from_a_perturbed_basis(form):
+    """psi = V beta_{:,j+1} to rounding after a push from a basis with orthogonality defect 1e-6
+    (the second projection's coefficients are summed into h); a residual of order 1e-6 would mean
+    the sum h + s was dropped."""
+    r = _step_from_perturbed_basis(oracle.lib(), form)
+    print(form, "relative residual", r)
+    assert r <= 1e3 * U64
 
 
 def _pins_pass(library):
@@ -528,6 +572,8 @@ def _form_pins_pass(library, form):
         if np.linalg.norm(np.eye(q2) - V2.T @ V2, 2) > 10 * 10 * U64:
             return False
         if np.linalg.norm(X2[:, :q2] - V2 @ B2) > 10 * 10 * U64 * np.linalg.norm(X2[:, :q2]):
+            return False
+        if _step_from_perturbed_basis(library, form) > 1e3 * U64:
             return False
         return True
     except Exception:
