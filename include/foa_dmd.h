@@ -134,9 +134,11 @@ int foa_dmd_push_batch(foa_dmd_t *h, const void *X_dev, int32_t p, int64_t ld,
 /*
  * Push one snapshot held in host memory: copies x_host (n elements of the handle's dtype;
  * pinned memory from foa_dmd_host_alloc gives full copy bandwidth) to a device staging
- * buffer on the handle's stream, then pushes it as foa_dmd_push does.  The call returns once
- * the copy is enqueued; x_host must stay valid until the handle's stream has passed the copy
- * (any later synchronising call, or foa_dmd_sync).
+ * buffer on the handle's stream, then pushes it as foa_dmd_push does.  Before enqueueing the
+ * copy the calling thread reads one byte per host page of x_host (pinned pages left unused for
+ * seconds otherwise copy at a fraction of the link's rate).  The call returns once the copy is
+ * enqueued; x_host must stay valid until the handle's stream has passed the copy (any later
+ * synchronising call, or foa_dmd_sync).
  */
 int foa_dmd_push_host(foa_dmd_t *h, const void *x_host, foa_dmd_push_info *info);
 
