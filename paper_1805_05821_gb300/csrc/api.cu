@@ -452,7 +452,15 @@ extern "C" int foa_dmd_push_batch(foa_dmd_t *h, const void *X_dev, int32_t p, in
 // instead of 208 GB/s, which made the first pushes of a 103 GB stream copy-bound (37.7 against
 // 41.8 snapshots/s from device memory); a CPU read of each page shortly before its copy restored
 // the full copy rate (41.3 snapshots/s).  The reads cost about a millisecond per 268 MB snapshot.
+// Only host memory (pinned or not) is read: a device or managed pointer is left to the copy,
+// which reports it.
 static void touch_host_pages(const void *p, size_t bytes) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  if (at.type != cudaMemoryTypeHost && at.type != cudaMemoryTypeUnregistered) return;
   static const size_t page = sysconf(_SC_PAGESIZE) > 0 ? size_t(sysconf(_SC_PAGESIZE)) : 4096;
   const volatile unsigned char *c = static_cast<const volatile unsigned char *>(p);
   unsigned char acc = 0;

@@ -267,3 +267,41 @@ def test_widest_basis_register_stage(dt, reorth):
     o, sts = run_oracle(Xr, N, dt, reorth=reorth)
     assert [s[0] for s in infos] == [0] * N and all(s[0] == "ok" for s in sts)
     compare_state(g, o, dt, with_basis=True, label=f"widest n=4097 reorth={reorth}")
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_push_host_matches_device_pushes(dt):
+    """foa_dmd_push_host from pinned memory (foa_dmd_host_alloc) and from pageable host memory
+    gives the state of foa_dmd_push on the same snapshots bit for bit (the host path adds only the
+    staged copy and the host-side page reads); n = 9001 (ragged last tile), N = 24 Gaussian."""
+    import ctypes
+    import torch
+    from paper_1805_05821_gb300 import foa_dmd as F
+    from paper_1805_05821_gb300.foa_dmd import FoaDMD
+    n, N = 9001, 24
+    X = gaussian(n, N, 24)
+    Xr, Xd = to_device(X, dt)
+    es = 4 if dt == "f32" else 2
+    gd = FoaDMD(n, N, dt)
+    for t in range(N):
+        gd.push(Xd[t], info=False)
+    want = gd.state()
+    Vd = gd.basis(0, N).cpu()
+    host_rows = Xd.cpu().contiguous()
+    ptr = F.foa_dmd_host_alloc(N * n * es)
+    try:
+        ctypes.memmove(ptr, host_rows.data_ptr(), N * n * es)
+        for label, base in (("pinned", ptr), ("pageable", host_rows.data_ptr())):
+            g = FoaDMD(n, N, dt)
+            for t in range(N):
+                st, _ = F.foa_dmd_push_host(g.h, base + t * n * es)
+                assert st == 0, (label, t, st)
+            q, stopped, H, B = g.state()
+            assert q == want[0] == N and not stopped
+            np.testing.assert_array_equal(H, want[2], err_msg=label)
+            np.testing.assert_array_equal(B, want[3], err_msg=label)
+            assert torch.equal(g.basis(0, N).cpu(), Vd), label
+            g.close()
+    finally:
+        F.foa_dmd_host_free(ptr)
+    gd.close()
