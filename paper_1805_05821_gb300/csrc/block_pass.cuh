@@ -19,8 +19,9 @@
 //                 outputs it receives as compensated (Kahan) FP32 pairs, widened to FP64 once.
 // Columns c >= j read column j - 1 instead (no predicated loads): the row sweep's coefficients are
 // zero there and the column sweep never writes those outputs.  Packed FMAs (__ffma2_rn) round each
-// lane like fmaf.  The cross-CTA reduction is deterministic
-// (fixed CTA groups); the last CTA finishes the pass (coefficients, norms, the first Cholesky step).
+// lane like fmaf.  The cross-CTA reduction is deterministic (fixed CTA groups); the last CTA
+// finishes the pass (coefficients, norms, the first Cholesky step).  A bounded wait that runs out
+// records FOA_DMD_ETIMEOUT in the block state, stops the refills and lets the CTA run to its end.
 #pragma once
 #include <type_traits>
 
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(T, 512 / T) block_pass_kernel(const BlockArgs 
       issue(k, t);
     }
 
-  // this thread's columns: c_u = g + G1 u (those below j)
+  // this thread's columns: c_u = g + G1 u (those below j are real)
   float2 acc[kCol ? FC * KP : 1];  // column sweep: (output 2kp, output 2kp+1) of column c_u
 #pragma unroll
   for (int i = 0; i < (kCol ? FC * KP : 1); ++i) acc[i] = make_float2(0.f, 0.f);
