@@ -33,7 +33,7 @@ def compare(g, o, dt, k_max=None, label="block push"):
     return compare_state(g, o, dt, with_basis=True, label=label)
 
 
-@pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4)])
+@pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4), ("bf16", 2)])
 def test_block_push_matches_oracle(dt, block):
     """n = 4900 (ragged last tile), 25 snapshots = 1 + 6 blocks of 4: damped waves on a 70^2 grid
     for FP32 (kappa_2 = 14), Gaussian snapshots for BF16."""
@@ -161,7 +161,7 @@ def test_block_push_stops_at_its_resolution_limit_on_fields():
     assert err <= 1e-6
 
 
-@pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4)])
+@pytest.mark.parametrize("dt,block", [("f32", 4), ("f32", 2), ("bf16", 4), ("bf16", 2)])
 def test_block_push_widest_basis(dt, block):
     """n = 4097 Gaussian snapshots (ragged last tile), N = 421 = 1 + 105 blocks of 4: the block
     passes run in every shape (256-thread CTAs with two, four or eight columns a thread up to
