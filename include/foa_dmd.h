@@ -346,6 +346,17 @@ int foa_dmd_autotune(foa_dmd_t *h, const char *cache_path, int32_t flags);
 int foa_dmd_tuned_geometry(foa_dmd_t *h, int32_t kind, int32_t j, int64_t *stage_bytes, int64_t *inflight_bytes,
                            int32_t *ctas_per_sm, int32_t *variant, int32_t *tuned);
 
+/*
+ * Self-checking builds (the library compiled with -DFOA_DMD_CHECKED, the stand-in for a memory
+ * checker): waits for the device, then returns in *bits the checks that failed since the last
+ * call and clears them: 1 = a bulk copy's shared-memory destination outside the CTA's shared
+ * window, 2 = a bulk copy's address or size not 16-byte aligned (or its mbarrier not 8-byte
+ * aligned), 4 = a streaming pass's tile index outside the tile count.  A failed check skips the
+ * access (the pipeline that misses it ends in its bounded wait with FOA_DMD_ETIMEOUT), so nothing
+ * faults.  In a normal build *bits = 0 and the call returns FOA_DMD_EINVAL.
+ */
+int foa_dmd_check_status(uint32_t *bits);
+
 /* Pinned host memory for foa_dmd_push_host (cudaHostAlloc / cudaFreeHost). */
 int foa_dmd_host_alloc(size_t bytes, void **ptr);
 int foa_dmd_host_free(void *ptr);

@@ -16,6 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfoa_dmd.so")
+# the self-checking variant (-DFOA_DMD_CHECKED: bounds and alignment checks on every bulk copy and
+# tile index, reported by foa_dmd_check_status), built on request into its own folder
+CHECKED_BUILD = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_BUILD, "libfoa_dmd_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -37,15 +41,19 @@ def _stale(obj, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra=None):
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=None, checked=False):
+    """Compile every .cu under csrc/ and link the library; returns its path.  checked=True builds
+    the self-checking variant into CHECKED_BUILD."""
+    bdir, lib = (CHECKED_BUILD, CHECKED_LIB) if checked else (BUILD, LIB)
+    extra = list(extra or []) + (["-DFOA_DMD_CHECKED"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-             "--expt-relaxed-constexpr"] + ARCH + (extra or [])
+             "--expt-relaxed-constexpr"] + ARCH + extra
     jobs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         if force or _stale(obj, [src] + headers):
             jobs.append((src, obj))
 
@@ -62,17 +70,17 @@ def build(force=False, verbose=False, extra=None):
                     sys.stderr.write(out)
                 if rc:
                     raise RuntimeError(f"nvcc failed for {src}")
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in sources()]
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in sources()]
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode:
             sys.stderr.write(p.stdout + p.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

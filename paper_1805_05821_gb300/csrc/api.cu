@@ -447,6 +447,33 @@ extern "C" int foa_dmd_push_batch(foa_dmd_t *h, const void *X_dev, int32_t p, in
   return FOA_DMD_OK;
 }
 
+// Check words of the translation units of a self-checking build, registered at load time.
+static std::vector<cudaError_t (*)(unsigned *)> &check_readers() {
+  static std::vector<cudaError_t (*)(unsigned *)> r;
+  return r;
+}
+namespace foa {
+int foa_check_register(cudaError_t (*read_and_clear)(unsigned *)) {
+  check_readers().push_back(read_and_clear);
+  return int(check_readers().size());
+}
+}  // namespace foa
+
+extern "C" int foa_dmd_check_status(uint32_t *bits) {
+  if (!bits) return FOA_DMD_EINVAL;
+  *bits = 0;
+#ifdef FOA_DMD_CHECKED
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned v = 0;
+  for (auto rd : check_readers())
+    if (e == cudaSuccess) e = rd(&v);
+  *bits = v;
+  return cuda_status(e);
+#else
+  return FOA_DMD_EINVAL;  // no checks compiled into this build
+#endif
+}
+
 // One read per host page of [p, p + bytes) on the calling thread.  Measured on GB300 (Grace host,
 // 64 KB pages): copies out of pinned pages that had gone unused for seconds ran at 9-37 GB/s
 // instead of 208 GB/s, which made the first pushes of a 103 GB stream copy-bound (37.7 against

@@ -227,7 +227,7 @@ __device__ __forceinline__ void run_stages(const BatchArgs &a, const StreamDesc 
     const uint32_t bbytes = bb ? uint32_t(nt) * kTile * (base_x ? uint32_t(sizeof(S)) : 4u) : 0u;
     unsigned char *dst = slots + size_t(slot) * ig.slot_bytes;
     mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * ig.tile_bytes + bbytes);
-    if (ig.tile_bytes)
+    if (ig.tile_bytes && FOA_CHECK(t0 >= 0 && t0 + nt <= sd.ntiles, kChkTile))
       for (int q = 0; q < nt; ++q)
         bulk_g2s(dst + size_t(q) * ig.tile_bytes, Vs + int64_t(t0 + q) * ig.tile_elems, ig.tile_bytes, &full[slot]);
     if (bbytes) {

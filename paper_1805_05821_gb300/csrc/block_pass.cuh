@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(T, 512 / T) block_pass_kernel(const BlockArgs 
     const uint32_t bbytes = base_bulk(t) ? uint32_t(kTile * sizeof(BaseT)) : 0u;
     unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
     mbar_arrive_expect_tx(&full[slot], tile_bytes + P * bbytes);
-    bulk_g2s(dst, Vg + int64_t(t) * tile_elems, tile_bytes, &full[slot]);
+    if (FOA_CHECK(t >= 0 && t < a.ntiles, kChkTile)) bulk_g2s(dst, Vg + int64_t(t) * tile_elems, tile_bytes, &full[slot]);
     if (bbytes)
       for (int k = 0; k < P; ++k)
         bulk_g2s(dst + a.base_off + k * a.base_stride, bg + k * bld + int64_t(t) * kTile, bbytes, &full[slot]);

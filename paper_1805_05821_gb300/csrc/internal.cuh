@@ -122,8 +122,49 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     if (clock64() - t0 > (1ll << 31)) return false;
   }
 }
+// ------------------------------------------------------------------------------------------
+// Self-checking build (compiled with -DFOA_DMD_CHECKED; build.build(checked=True)): every bulk
+// copy checks its shared-memory destination against the CTA's shared window and the 16-byte
+// alignment of both addresses and of the size, and the streaming producers check each tile index
+// against the tile count.  A failed check sets a bit in this translation unit's check word
+// (foa_dmd_check_status ORs the words of all units) and skips the access, so nothing faults: the
+// pipeline that misses the copy ends in its bounded wait.  Without the macro the checks vanish.
+// ------------------------------------------------------------------------------------------
+enum CheckBits : unsigned { kChkSmem = 1u, kChkAlign = 2u, kChkTile = 4u };
+#ifdef FOA_DMD_CHECKED
+static __device__ unsigned foa_check_word;
+__device__ __forceinline__ bool foa_check(bool ok, unsigned bit) {
+  if (!ok) atomicOr(&foa_check_word, bit);
+  return ok;
+}
+int foa_check_register(cudaError_t (*read_and_clear)(unsigned *));
+static cudaError_t foa_check_read_unit(unsigned *out) {
+  unsigned v = 0, z = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, foa_check_word, sizeof(v));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(foa_check_word, &z, sizeof(z));
+  *out |= v;
+  return e;
+}
+static const int foa_check_registered_ = foa_check_register(&foa_check_read_unit);
+#define FOA_CHECK(cond, bit) foa_check((cond), (bit))
+#else
+#define FOA_CHECK(cond, bit) true
+#endif
+
 // One-dimensional bulk copy global -> shared, completing on an mbarrier (transaction bytes).
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+#ifdef FOA_DMD_CHECKED
+  {
+    uint32_t total;
+    asm("mov.u32 %0, %%total_smem_size;" : "=r"(total));
+    const uint32_t d = smem_addr(dst);
+    if (!FOA_CHECK(((d | uint32_t(reinterpret_cast<uintptr_t>(src)) | bytes) & 15u) == 0 && bytes != 0 &&
+                       (smem_addr(bar) & 7u) == 0,
+                   kChkAlign))
+      return;
+    if (!FOA_CHECK(uint64_t(d) + bytes <= total, kChkSmem)) return;
+  }
+#endif
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                    smem_addr(dst)),
                "l"(src), "r"(bytes), "r"(smem_addr(bar))

@@ -153,8 +153,9 @@ __global__ void __launch_bounds__(kThreads, 2) lag_ws_kernel(const PassArgs a) {
         const uint32_t wbytes = pend ? uint32_t(nt) * kTile * 4u : 0u;
         unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
         mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + xbytes + wbytes);
-        for (int k = 0; k < nt; ++k)
-          bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
+        if (FOA_CHECK(t0 >= 0 && t0 + nt <= a.ntiles, kChkTile))
+          for (int k = 0; k < nt; ++k)
+            bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
         if (xbytes) bulk_g2s(dst + a.base_off, xg + r0, xbytes, &full[slot]);
         if (wbytes) bulk_g2s(dst + a.base2_off, wg + r0, wbytes, &full[slot]);
       }

@@ -348,8 +348,9 @@ __global__ void __launch_bounds__(kThreads, pass_min_blocks<S, NC>()) pass_kerne
         unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
         mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
         if (tile_bytes) {
-          for (int k = 0; k < nt; ++k)
-            bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
+          if (FOA_CHECK(t0 >= 0 && t0 + nt <= a.ntiles, kChkTile))
+            for (int k = 0; k < nt; ++k)
+              bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
         }
         if (bbytes) bulk_g2s(dst + a.base_off, baseg + r0, bbytes, &full[slot]);
         sflag[1] = it + 1;

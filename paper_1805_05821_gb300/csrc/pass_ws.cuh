@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(kThreads, 2) pass_ws_kernel(const PassArgs a) 
         const uint32_t bbytes = base_bulk ? uint32_t(nt) * kTile * sizeof(BaseT) : 0u;
         unsigned char *dst = slots + size_t(slot) * a.slot_bytes;
         mbar_arrive_expect_tx(&full[slot], uint32_t(nt) * tile_bytes + bbytes);
-        for (int k = 0; k < nt; ++k)
-          bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
+        if (FOA_CHECK(t0 >= 0 && t0 + nt <= a.ntiles, kChkTile))
+          for (int k = 0; k < nt; ++k)
+            bulk_g2s(dst + size_t(k) * tile_bytes, Vg + int64_t(t0 + k) * tile_elems, tile_bytes, &full[slot]);
         if (bbytes) bulk_g2s(dst + a.base_off, baseg + r0, bbytes, &full[slot]);
       }
     }

@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-_LIB_PATH = _build.LIB
+# FOA_DMD_CHECKED=1 loads the self-checking build (build.build(checked=True)) instead
+_LIB_PATH = _build.CHECKED_LIB if os.environ.get("FOA_DMD_CHECKED") == "1" else _build.LIB
 
 F64, F32, BF16 = 0, 1, 2
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16}
@@ -76,6 +77,7 @@ def lib():
                                                   ctypes.POINTER(i32)]),
             "foa_dmd_eig": (ctypes.c_int, [vp, d, ctypes.POINTER(foa_dmd_eig_result)]),
             "foa_dmd_test_wait_fault": (ctypes.c_int, [vp, i32, i64]),
+            "foa_dmd_check_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
             "foa_dmd_get_state": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), _DP, _DP, i32]),
             "foa_dmd_get_basis": (ctypes.c_int, [vp, i32, i32, vp, i64]),
             "foa_dmd_reset": (ctypes.c_int, [vp]),
@@ -229,6 +231,14 @@ def foa_dmd_eig(h, rank_tol, cap, n_modes=0, phi=None, ld_phi=0, vec_cols=0, wan
             m = res.m
             out["vec"] = (vr[:m * vc].reshape(vc, m).T + 1j * vi[:m * vc].reshape(vc, m).T)
     return out
+
+
+def foa_dmd_check_status():
+    """(status, bits): the device checks that failed since the last call in a self-checking build
+    (status EINVAL in a normal build)."""
+    bits = ctypes.c_uint32(0)
+    st = lib().foa_dmd_check_status(ctypes.byref(bits))
+    return st, bits.value
 
 
 def foa_dmd_test_wait_fault(h, skip_cta, spin_cycles):
