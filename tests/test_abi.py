@@ -68,3 +68,17 @@ def test_no_cpu_fallback(L):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert L.foa_dmd_create(100, 8, 1, None, ctypes.byref(h)) == foa_dmd.ECUDA
+
+
+def test_checked_build_translation_units_compile(tmp_path):
+    """The self-checking variant (-DFOA_DMD_CHECKED) still compiles: the unit holding the check
+    registry and foa_dmd_check_status, and units of the single, block and batched passes (nvcc
+    cross-compiles without a GPU; the GPU test builds and runs the whole variant)."""
+    import subprocess
+    csrc = os.path.join(ROOT, "paper_1805_05821_gb300", "csrc")
+    flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", csrc,
+             "--expt-relaxed-constexpr", "-DFOA_DMD_CHECKED"] + build.ARCH
+    for unit in ("api.cu", "pass_f32.cu", "block_pass_f32.cu", "batch.cu"):
+        p = subprocess.run([build.nvcc(), "-c", os.path.join(csrc, unit), "-o", str(tmp_path / (unit + ".o"))] + flags,
+                           capture_output=True, text=True)
+        assert p.returncode == 0, (unit, p.stderr[-2000:])
