@@ -256,12 +256,14 @@ int foa_dmd_load(const char *path, const foa_dmd_opts *opts, foa_dmd_t **out);
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
  * should therefore come before any stream capture.  Every call shares the array and clears
  * what must start at zero; calls that overlap on the GPU (different streams or threads) race
- * on it.  The call synchronises cuda_stream before returning.  There is no handle to remember
- * a breakdown: the caller's H-bar is the record.  A breakdown (EBREAKDOWN) writes h into H-bar
- * column q (1-based) and leaves q alone; a later call with that q finds the column non-zero and
- * returns ESTOPPED without changing anything (a zero first snapshot records nothing, so a call
- * after it starts the stream afresh).  Errors: EINVAL (sizes beyond the limits, null pointers),
- * EFULL, EBREAKDOWN, ESTOPPED, ENONFINITE, ETIMEOUT, ECUDA.
+ * on it.  The call synchronises cuda_stream before returning, so it cannot be part of a stream
+ * capture: while cuda_stream is being captured it returns EINVAL without enqueueing anything.
+ * There is no handle to remember a breakdown: the caller's H-bar is the record.  A breakdown
+ * (EBREAKDOWN) writes h into H-bar column q (1-based) and leaves q alone; a later call with that
+ * q finds the column non-zero and returns ESTOPPED without changing anything (a zero first
+ * snapshot records nothing, so a call after it starts the stream afresh).  Errors: EINVAL (sizes
+ * beyond the limits, null pointers, a capturing stream), EFULL, EBREAKDOWN, ESTOPPED, ENONFINITE,
+ * ETIMEOUT, ECUDA.
  */
 int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, void *V, double *Hbar, double *beta,
                          int32_t q, const void *x_dev, void *w_dev, double breakdown_tol, void *cuda_stream,

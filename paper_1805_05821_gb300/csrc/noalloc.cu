@@ -61,6 +61,12 @@ extern "C" int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, voi
   int sms = 0;
   int rc = check_device(&sms);
   if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  // the call synchronises its stream and copies to pageable host memory, neither of which a
+  // stream capture allows: refuse before anything is enqueued
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &capture) != cudaSuccess || capture != cudaStreamCaptureStatusNone)
+    return FOA_DMD_EINVAL;
   if (!g_addr[dev]) {
     // first call on this device: resolve the array's device address (must precede any capture)
     void *p = nullptr;
@@ -73,7 +79,6 @@ extern "C" int foa_dmd_push_noalloc(int64_t n, int32_t k_max, int32_t dtype, voi
   double *partials = reinterpret_cast<double *>(base + kStateBytes + kVecBytes);
   double *gpart = reinterpret_cast<double *>(base + kStateBytes + kVecBytes + kPartBytes);
   uint32_t *gcount = reinterpret_cast<uint32_t *>(base + kStateBytes + kVecBytes + kPartBytes + kGpartBytes);
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
 
   // A stand-in handle that points at the caller's buffers and the static scratch.
   foa_dmd h;

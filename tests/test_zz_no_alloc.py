@@ -115,3 +115,33 @@ def test_noalloc_breakdown_then_stopped():
     st, info = F.foa_dmd_push_noalloc(n, K, "f64", V, H, B, q, X[11], w)
     assert st == F.ESTOPPED and info.q == 10
     assert torch.equal(H, Hb) and torch.equal(B, Bb) and torch.equal(V, Vb)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call synchronises its stream, which a stream capture does not allow: on a stream that is
+    being captured it returns EINVAL before enqueueing anything, and the caller's buffers stay
+    untouched (the capture itself goes on: the work after the call is captured as usual)."""
+    import torch
+    from paper_1805_05821_gb300 import build
+    from paper_1805_05821_gb300 import foa_dmd as F
+    build.build()
+    n, K = 4096, 16
+    V, H, B, w, _ = _buffers(n, K, "f32")
+    x = torch.randn(n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        st, _ = F.foa_dmd_push_noalloc(n, K, "f32", V, H, B, 0, x, w, stream=s)
+        y = x * 2.0
+    torch.cuda.synchronize()
+    assert st == F.EINVAL
+    assert int(torch.count_nonzero(H)) == 0 and int(torch.count_nonzero(B)) == 0
+    assert int(torch.count_nonzero(V)) == 0 and int(torch.count_nonzero(w)) == 0
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, x * 2.0)
+    # outside a capture the same call pushes
+    st, info = F.foa_dmd_push_noalloc(n, K, "f32", V, H, B, 0, x, w, stream=s)
+    s.synchronize()
+    assert st == 0 and info.q == 1
